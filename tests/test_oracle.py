@@ -1,0 +1,254 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: values
+printed in the paper, closed forms, the exact spectrum of the harmonic
+oscillator, dense matrices built from the DFT definition, or the convergence
+order that the paper states.
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from itp_workloads import (Grid, cubic, gaussian_wells_potential,
+                           harmonic_potential, normal_states)
+from oracle import dense_reference as D
+from oracle import itp_oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# --- Eq. (coef) against the printed Eqs. (four)-(ten) -----------------------
+def test_coefficients_match_printed_expansions():
+    rows = _read_golden("mp_coefficients.txt")
+    assert len(rows) == 4
+    for row in rows:
+        k = int(row[0])
+        printed = [Fraction(s) for s in row[1:]]
+        assert len(printed) == k
+        assert O.mp_coefficients(k) == printed
+
+
+@pytest.mark.parametrize("k", range(1, 9))
+def test_coefficients_remove_odd_orders(k):
+    """Eq. (secerr): T_2(eps/i)^i = exp(eps H + eps^3 E_3 / i^2 + ...), so
+    the expansion is exact through order 2k iff sum_i c_i = 1 and
+    sum_i c_i i^(-2m) = 0 for m = 1..k-1."""
+    c = O.mp_coefficients(k)
+    assert sum(c) == 1
+    for m in range(1, k):
+        assert sum(ci / Fraction(i) ** (2 * m) for i, ci in enumerate(c, 1)) == 0
+    if k > 1:  # and the next order survives (the expansion is not higher order)
+        assert sum(ci / Fraction(i) ** (2 * k) for i, ci in enumerate(c, 1)) != 0
+
+
+def test_order12_coefficients_closed_form():
+    """Order 12 (k = 6) is not printed; the closed form must still give the
+    odd-order-free expansion, and the signs alternate as in Eqs. (four)-(ten)."""
+    c = O.mp_coefficients(6)
+    assert [1 if x > 0 else -1 for x in c] == [-1, 1, -1, 1, -1, 1]
+    assert c[0] == Fraction(-1, 302400)
+
+
+def test_fft_counts():
+    for order, count in _read_golden("fft_counts.txt"):
+        assert O.fft_count(int(order) // 2) == int(count)
+
+
+# --- Eq. (so) against dense matrices built from the DFT definition ----------
+def test_t2_matches_dense_operator_nonseparable():
+    """T_2 on a non-cubic grid with a random potential equals the dense
+    diag(e^{-tau V/2}) (Pz x Py x Px) diag(e^{-tau V/2}) built without FFTs."""
+    g = Grid(6, 4, 8, 5.0, 3.0, 7.0)
+    rng = np.random.default_rng(7)
+    V = rng.uniform(-1.0, 1.0, g.shape)
+    psi = rng.standard_normal(g.shape)
+    tau = 0.37
+    k2 = O.kinetic_k2(g.shape, (g.lz, g.ly, g.lx))
+    got = O.t2(psi, V, tau, k2).ravel()
+    want = D.dense_t2(g, V, tau) @ psi.ravel()
+    assert np.max(np.abs(got - want)) < 1e-13 * np.max(np.abs(want))
+
+
+def test_apply_h_matches_dense_hamiltonian():
+    g = Grid(4, 6, 6, 4.0, 5.0, 3.0)
+    rng = np.random.default_rng(3)
+    V = rng.uniform(-2.0, 2.0, g.shape)
+    psi = rng.standard_normal(g.shape)
+    k2 = O.kinetic_k2(g.shape, (g.lz, g.ly, g.lx))
+    got = O.apply_h(psi, V, k2).ravel()
+    want = D.dense_hamiltonian(g, V) @ psi.ravel()
+    assert np.max(np.abs(got - want)) < 1e-12 * np.max(np.abs(want))
+
+
+def test_t2k_reduces_to_t2_for_order2():
+    g = Grid(4, 4, 6, 3.0, 3.0, 4.0)
+    rng = np.random.default_rng(1)
+    V = rng.uniform(-1, 1, g.shape)
+    psi = rng.standard_normal(g.shape)
+    k2 = O.kinetic_k2(g.shape, (g.lz, g.ly, g.lx))
+    assert np.array_equal(O.t2k(psi, V, 0.3, k2, 1), O.t2(psi, V, 0.3, k2))
+
+
+# --- spectrum of the harmonic oscillator -------------------------------------
+def test_ho_grid_spectrum_is_exact():
+    """On 32^3 / [-8,8)^3 the spectral grid Hamiltonian of V = r^2/2 has the
+    continuum spectrum E = n + 3/2 with degeneracies 1, 3, 6 to round-off."""
+    g = cubic(32, 16.0)
+    E = D.ho_grid_spectrum(g, 10)
+    want = np.array([1.5] + [2.5] * 3 + [3.5] * 6)
+    assert np.max(np.abs(E - want)) < 1e-12
+
+
+def test_ho_itp_converges_to_exact_spectrum():
+    """The iteration (Eqs. 3, 4) with the order-4 expansion, tau = 0.1, from
+    random-normal states finds 1, 3, 6 levels at 3/2, 5/2, 7/2."""
+    g = cubic(32, 16.0)
+    V = harmonic_potential(g)
+    psi0 = normal_states(12, g.n_points, seed=1234)
+    E, Psi, it = O.solve(psi0, V, g, 4, 0.1, n_report=10, tol=1e-12,
+                         max_iter=400)
+    want = np.array([1.5] + [2.5] * 3 + [3.5] * 6)
+    assert it < 400
+    assert np.max(np.abs(E[:10] - want)) < 1e-10
+    ov = Psi @ Psi.T * g.dV
+    assert np.max(np.abs(ov - np.eye(len(Psi)))) < 1e-12
+
+
+# --- brute force on a tiny grid ---------------------------------------------
+def _tiny_wells():
+    g = Grid(8, 8, 6, 6.0, 6.0, 5.0)
+    centres = np.array([[0.8, 0.0, 0.3], [-1.1, 0.7, -0.2], [0.2, -1.0, 0.9]])
+    V = gaussian_wells_potential(g, centres, [3.0, 2.0, 2.5], [0.8, 0.7, 0.9])
+    return g, V
+
+
+def test_itp_matches_dense_diagonalisation_tiny_grid():
+    g, V = _tiny_wells()
+    H = D.dense_hamiltonian(g, V)
+    E_ref = np.linalg.eigvalsh(H)[:6]
+    psi0 = normal_states(9, g.n_points, seed=99)
+    E, Psi, it = O.solve(psi0, V, g, 8, 0.2, n_report=6, tol=1e-13,
+                         max_iter=3000)
+    assert np.max(np.abs(E[:6] - E_ref)) < 1e-10
+
+
+# --- convergence order (Fig. 1: error ~ Delta t^order) -----------------------
+@pytest.mark.parametrize("order", [2, 4, 6, 8, 10, 12])
+def test_propagator_eigenvalue_order(order):
+    """The propagator eigenvalue E_T = -ln(psi|T_2k(tau)|psi)/tau of the exact
+    ground state deviates from E_0 as tau^(2k) (Fig. 1's Delta t^n lines).
+
+    The windows sit where the error is far above FP64 round-off; the
+    higher odd-order terms of Eq. (secerr) make the approach to the
+    asymptotic slope slow, so orders 10 and 12 are only required to beat the
+    next lower order clearly.  A wrong or missing coefficient drops the order
+    to 2 or 0 and fails every case.
+    """
+    g, V = _tiny_wells()
+    w, U = np.linalg.eigh(D.dense_hamiltonian(g, V))
+    psi = U[:, 0] / np.sqrt(g.dV)
+    taus = {2: [0.1, 0.05, 0.025], 4: [0.1, 0.05, 0.025],
+            6: [0.15, 0.1, 0.05], 8: [0.2, 0.15, 0.1],
+            10: [0.4, 0.3, 0.2], 12: [0.6, 0.4, 0.3]}[order]
+    err = [abs(O.propagator_eigenvalue(psi, V, g, order, t) - w[0]) for t in taus]
+    assert min(err) > 2e-12
+    slope = np.polyfit(np.log(taus), np.log(err), 1)[0]
+    if order <= 8:
+        assert abs(slope - order) < 0.75, (slope, err)
+    else:
+        assert order - 3.0 < slope < order + 0.5, (slope, err)
+
+
+def _exact_propagator(g, V):
+    """e^{-tau H} psi from the dense eigen-decomposition of the grid H."""
+    w, U = np.linalg.eigh(D.dense_hamiltonian(g, V))
+    return w, U, lambda psi, t: (U @ (np.exp(-t * w) * (U.T @ psi.ravel()))).reshape(g.shape)
+
+
+@pytest.mark.parametrize("order,taus", [(2, [0.05, 0.025, 0.0125]),
+                                        (4, [0.05, 0.025, 0.0125]),
+                                        (6, [0.1, 0.05, 0.025]),
+                                        (8, [0.2, 0.1, 0.05])])
+def test_local_error_of_t2k(order, taus):
+    """Eq. (mcomp): T_2k(tau) = e^{-tau H} + O(tau^(2k+1)), against the exact
+    propagator of the dense grid Hamiltonian, on a smooth state."""
+    g, V = _tiny_wells()
+    w, U, exact = _exact_propagator(g, V)
+    psi = (U[:, :6] @ np.array([1, .5, .4, .3, .2, .1]) / np.sqrt(g.dV)).reshape(g.shape)
+    k2 = O.kinetic_k2(g.shape, (g.lz, g.ly, g.lx))
+    d = [np.linalg.norm(O.t2k(psi, V, t, k2, order // 2) - exact(psi, t))
+         / np.linalg.norm(psi) for t in taus]
+    assert min(d) > 1e-13
+    slope = np.polyfit(np.log(taus), np.log(d), 1)[0]
+    # order 8 is still approaching its asymptote above the round-off floor:
+    # require it to beat order 6's tau^7 clearly
+    tol = 0.5 if order < 8 else 0.95
+    assert abs(slope - (order + 1)) < tol, (slope, d)
+
+
+def test_romberg_extrapolation_of_multiproduct_t4():
+    """Eq. (sixp) cancels the tau^5 term of T_4.  The multi-product T_4 is a
+    sum of products, not time-symmetric, so its tau^6 term is not tied to the
+    tau^5 term and survives: the local error falls as tau^6, one order better
+    than T_4 (tau^5) and one order short of the multi-product T_6 (tau^7)."""
+    g, V = _tiny_wells()
+    w, U, exact = _exact_propagator(g, V)
+    psi = (U[:, :6] @ np.array([1, .5, .4, .3, .2, .1]) / np.sqrt(g.dV)).reshape(g.shape)
+    k2 = O.kinetic_k2(g.shape, (g.lz, g.ly, g.lx))
+    taus = [0.05, 0.025, 0.0125]
+    d = [np.linalg.norm(O.romberg_t6(psi, V, t, k2) - exact(psi, t)) for t in taus]
+    slope = np.polyfit(np.log(taus), np.log(d), 1)[0]
+    assert abs(slope - 6.0) < 0.3, (slope, d)
+
+
+# --- Eq. (4): orthonormalisation ---------------------------------------------
+def test_cholesky_orthonormalize_is_gram_schmidt():
+    """psi = L^{-1} phi equals modified Gram-Schmidt of the rows in order
+    (both give the unique orthonormal basis with a positive triangular map)."""
+    rng = np.random.default_rng(11)
+    dV = 0.125
+    Phi = rng.standard_normal((7, 200))
+    Psi, L = O.cholesky_orthonormalize(Phi, dV)
+    Q = Phi.copy()
+    for j in range(len(Q)):
+        for i in range(j):
+            Q[j] -= (Q[j] @ Q[i]) * dV * Q[i]
+        Q[j] /= np.sqrt(Q[j] @ Q[j] * dV)
+    assert np.max(np.abs(Psi - Q)) < 1e-12
+    assert np.max(np.abs(Psi @ Psi.T * dV - np.eye(7))) < 1e-13
+    assert np.allclose(np.tril(L), L)
+
+
+def test_cholesky_rejects_rank_deficient():
+    rng = np.random.default_rng(2)
+    Phi = rng.standard_normal((4, 50))
+    Phi[3] = 0.0  # a vanished state: S has a zero pivot
+    with pytest.raises(np.linalg.LinAlgError):
+        O.cholesky_orthonormalize(Phi, 1.0)
+
+
+def test_ritz_rotation_preserves_trace_and_span():
+    g = cubic(8, 6.0)
+    V = harmonic_potential(g)
+    Psi, _ = O.cholesky_orthonormalize(normal_states(5, g.n_points, 4), g.dV)
+    E0, _, _ = O.energies(Psi, V, g, ritz=False)
+    E1, Psi1, HPsi1 = O.energies(Psi, V, g, ritz=True)
+    assert abs(E0.sum() - E1.sum()) < 1e-12 * abs(E0.sum())
+    P0 = Psi.T @ Psi
+    P1 = Psi1.T @ Psi1
+    assert np.max(np.abs(P0 - P1)) < 1e-12 * np.max(np.abs(P0))
+    # the rotated states diagonalise the subspace matrix
+    Hs = Psi1 @ HPsi1.T * g.dV
+    assert np.max(np.abs(Hs - np.diag(E1))) < 1e-12 * np.max(np.abs(E1))
