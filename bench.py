@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Throughput of the multi-product imaginary-time step on GB300.
+
+One step = itp_propagate (order-2k multi-product propagator on all states,
+Eq. 3) + itp_orthonormalize (Eq. 4) + itp_energies with the Ritz rotation.
+The metric is state-steps per second: (n + guard states) x steps / time.
+
+Default workload: the C60-like Gaussian well on a 128^3 grid (box 32 bohr),
+n = 120 wanted + 8 guard states, order 12, tau = 0.25, in the mixed form
+(FP32 FFT passes; FP64 combination, Cholesky and energies).  The FP64 form
+of the same workload is measured beside it.  Inputs are seeded and
+synthetic (itp_workloads).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (the reference arm; there is no other implementation to run).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+if "--impl" in sys.argv and "reference" in sys.argv or "--cpu-sample" in sys.argv:
+    # the oracle leg runs single-threaded (numpy FFT is; pin BLAS too)
+    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[_v] = "1"
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "c60_128": dict(n=128, box=32.0, potential="c60", n_states=120, n_guard=8, order=12,
+                    tau=0.25, seed=1234,
+                    desc="C60-like Gaussian well (60 wells, depth 2.0 Ha, sigma 0.8 bohr, "
+                         "radius 6.7 bohr), 128^3 grid, box 32 bohr, n=120 + 8 guard states, "
+                         "order 12 (k_i = 1..6), tau = 0.25"),
+    "ho_32": dict(n=32, box=16.0, potential="ho", n_states=10, n_guard=2, order=4, tau=0.1,
+                  seed=1234, desc="3D harmonic oscillator, 32^3 grid, box [-8,8)^3, n=10 + 2 "
+                                  "guard, order 4, tau = 0.1"),
+}
+
+
+def make_inputs(w, rank=0):
+    from itp_workloads import build_native, c60_like_potential, cubic, harmonic_potential, \
+        normal_states
+    try:
+        build_native()
+    except Exception:
+        pass
+    g = cubic(w["n"], w["box"])
+    V = c60_like_potential(g) if w["potential"] == "c60" else harmonic_potential(g)
+    m = w["n_states"] + w["n_guard"]
+    psi = normal_states(m, g.n_points, seed=w["seed"], problem=rank)
+    return g, V, psi
+
+
+def algorithmic_bytes(kind, g, m, s):
+    """Bytes a launch of `kind` must move over m states (s = bytes per real):
+    every pass reads and writes the half spectrum once; the potential factor
+    is read once per launch."""
+    N = g.n_points
+    Nh = g.nz * g.ny * (g.nx // 2 + 1)
+    spec = m * Nh * 2 * s
+    return {
+        "pencil": 2 * spec,
+        "plane_merged": 2 * spec + N * s,
+        "plane_fwd": m * N * s + N * s + spec,
+        "plane_combine": spec + N * s + 2 * m * N * 8,
+        "pencil_kinetic": 2 * spec,
+        "plane_hpsi": spec + m * N * s + N * 8 + m * N * 8,
+    }.get(kind)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id=None):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if gpu_id:
+            cmd.insert(1, f"--id={gpu_id}")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_sample(w, n_sample, steps):
+    """Time the FP64 oracle on n_sample states of the workload (one oracle
+    step per timed step).  Returns state-steps per second."""
+    from oracle import itp_oracle as O
+    from itp_workloads import c60_like_potential, cubic, harmonic_potential, normal_states
+    g = cubic(w["n"], w["box"])
+    V = c60_like_potential(g) if w["potential"] == "c60" else harmonic_potential(g)
+    psi = normal_states(n_sample, g.n_points, seed=w["seed"])
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        psi, E = O.itp_step(psi, V, g, w["order"], w["tau"], ritz=True)
+        times.append(time.perf_counter() - t0)
+    return n_sample / (sum(times) / len(times)), sum(times)
+
+
+def run_reference(args):
+    w = WORKLOADS[args.workload]
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n_sample = 1
+    from oracle import itp_oracle as O
+    from itp_workloads import c60_like_potential, cubic, harmonic_potential, normal_states
+    g = cubic(w["n"], w["box"])
+    V = c60_like_potential(g) if w["potential"] == "c60" else harmonic_potential(g)
+    psi = normal_states(n_sample, g.n_points, seed=w["seed"])
+    for _ in range(args.warmup):
+        psi, _ = O.itp_step(psi, V, g, w["order"], w["tau"], ritz=True)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        psi, _ = O.itp_step(psi, V, g, w["order"], w["tau"], ritz=True)
+    dt = time.perf_counter() - t0
+    value = n_sample * args.steps / dt
+    sample = (f"{n_sample} state(s) of the workload per step: the oracle's propagation, "
+              f"Cholesky and Ritz step on that block")
+    line = {
+        "impl": "reference", "metric": "state-steps/s", "value": value, "unit": "state-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["desc"], "precision": "fp64 (CPU oracle)"},
+        "cpu_baseline": {"value": value, "unit": "state-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "state-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def time_steps(h, stream, order, tau, steps, torch):
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    E = None
+    start.record(stream)
+    for _ in range(steps):
+        E = h.step(order, tau)
+    end.record(stream)
+    end.synchronize()
+    return start.elapsed_time(end) / 1e3, E
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c60_128", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path measurement")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+
+    if args.cpu_sample:
+        v, t = cpu_sample(w, 1, 2)
+        print(json.dumps({"value": v, "seconds": t}))
+        return
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    if args.warmup < 3:
+        raise SystemExit("timing rules: at least 3 warm-up steps")
+
+    import torch
+    import torch.distributed as dist
+    import paper_0809_3739_gb300 as P
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.Stream()
+    g, V, psi = make_inputs(w, rank)
+    m = w["n_states"] + w["n_guard"]
+    order, tau = w["order"], w["tau"]
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- headline: mixed path, states resident in HBM --------------------------
+    h = P.ItpGrid(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, w["n_states"], w["n_guard"],
+                  P.ITP_MIXED, cuda_stream=stream.cuda_stream)
+    h.set_potential(V)
+    h.set_states(psi)
+    for _ in range(args.warmup):
+        h.step(order, tau)
+    gpu_id = None
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(local).uuid)
+        if not gpu_id.startswith("GPU-"):
+            gpu_id = "GPU-" + gpu_id
+    except Exception:
+        gpu_id = None
+    barrier()
+    clocks = ClockSampler(gpu_id)
+    n0 = h.kernel_launches
+    h.profile(True)
+    dt, E = time_steps(h, stream, order, tau, args.steps, torch)
+    prof = h.profile_read()
+    h.profile(False)
+    launches = h.kernel_launches - n0
+    clk = clocks.stop()
+    barrier()
+    dt_t = torch.tensor([dt], device="cuda")
+    if world > 1:
+        dist.all_reduce(dt_t, op=dist.ReduceOp.MAX)
+    dt = float(dt_t.item())
+    value = world * m * args.steps / dt
+
+    # dominant kernel of the step and its roofline
+    kinds = {k: v for k, v in prof.items() if v[0] > 0}
+    top = max(kinds, key=lambda k: kinds[k][1])
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    roof = None
+    ab = algorithmic_bytes(top, g, m, 4)
+    if ab is not None:
+        per_launch_s = kinds[top][1] / 1e3 / kinds[top][0]
+        achieved = ab / per_launch_s / 1e9
+        roof = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": None, "algorithmic_bytes_per_launch": ab,
+                "avg_launch_ms": per_launch_s * 1e3}
+    total_prof = sum(v[1] for v in kinds.values())
+    breakdown = {k: {"launches": v[0], "ms": round(v[1], 3),
+                     "share": round(v[1] / total_prof, 4)} for k, v in kinds.items()}
+    h.close()
+
+    # ---- end to end through the C ABI with host buffers -----------------------
+    e2e = None
+    if not args.no_e2e:
+        K = min(args.steps, 5)
+        h = P.ItpGrid(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, w["n_states"], w["n_guard"],
+                      P.ITP_MIXED, cuda_stream=stream.cuda_stream)
+        h.set_potential(V)
+        pin_in = torch.from_numpy(psi).pin_memory()
+        pin_out = torch.empty_like(pin_in).pin_memory()
+        E_host = np.empty(m)
+        lib = P.load()
+        h.set_states(psi)
+        for _ in range(3):
+            h.step(order, tau)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            lib.itp_set_states(h.h, pin_in.data_ptr())
+            h.propagate(order, tau)
+            h.orthonormalize()
+            P.itp_energies(h.h, E_host, P.ITP_RITZ)
+            P.itp.load().itp_get_states(h.h, pin_out.data_ptr())
+        barrier()
+        t_e2e = time.perf_counter() - t0
+        e2e = {"value": world * m * K / t_e2e, "unit": "state-steps/s",
+               "h2d_bytes_per_step": int(psi.nbytes),
+               "d2h_bytes_per_step": int(psi.nbytes + E_host.nbytes), "steps": K}
+        h.close()
+
+    # ---- the FP64 form of the same workload -----------------------------------
+    fp64 = None
+    if not args.no_fp64:
+        K = min(args.steps, 3)
+        h = P.ItpGrid(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, w["n_states"], w["n_guard"],
+                      P.ITP_FP64, cuda_stream=stream.cuda_stream)
+        h.set_potential(V)
+        h.set_states(psi)
+        for _ in range(3):
+            h.step(order, tau)
+        barrier()
+        h.profile(True)
+        dt64, _ = time_steps(h, stream, order, tau, K, torch)
+        prof64 = {k: v for k, v in h.profile_read().items() if v[0] > 0}
+        tot64 = sum(v[1] for v in prof64.values())
+        fp64 = {"value": world * m * K / dt64, "unit": "state-steps/s", "steps": K,
+                "ms_per_step": 1e3 * dt64 / K,
+                "breakdown": {k: {"launches": v[0], "ms": round(v[1], 3),
+                                  "share": round(v[1] / tot64, 4)} for k, v in prof64.items()}}
+        h.close()
+
+    # ---- CPU oracle on a bounded sample (rank 0, N = 1 only) -------------------
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample",
+                            "--workload", args.workload], capture_output=True, text=True,
+                           timeout=900)
+        try:
+            res = json.loads(r.stdout.strip().splitlines()[-1])
+            cpu = {"value": res["value"], "unit": "state-steps/s", "cores": 1, "kind": "oracle",
+                   "sample": "1 state of the workload, 2 oracle steps (propagation, Cholesky, "
+                             f"Ritz), {res['seconds']:.1f} s of CPU work"}
+        except Exception:
+            cpu = {"value": None, "unit": "state-steps/s", "cores": 1, "kind": "oracle",
+                   "sample": "failed: " + (r.stderr.strip().splitlines() or ["?"])[-1]}
+
+    if rank == 0:
+        line = {
+            "metric": "state-steps/s", "value": value, "unit": "state-steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "mixed: f32 FFT passes, f64 combination/Cholesky/energies",
+            "data": "synthetic (seeded Philox4x32-10 states, C60-like potential)",
+            "config": {"workload": w["desc"], "precision": "mixed", "grid": w["n"],
+                       "box_bohr": w["box"], "n_states": w["n_states"],
+                       "n_guard": w["n_guard"], "order": order, "tau": tau,
+                       "l2": "inputs larger than L2 (FP32 state block "
+                             f"{m * g.n_points * 4 / 1e9:.2f} GB, half spectrum "
+                             f"{m * g.nz * g.ny * (g.nx // 2 + 1) * 8 / 1e9:.2f} GB)",
+                       "parallelism": f"replicas x{world} (independent problems)"},
+            "gpu_launches": launches,
+            "roofline": roof,
+            "kernel_breakdown": breakdown,
+            "fp64_path": fp64,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "energies_head": [round(float(x), 8) for x in E[:4]],
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

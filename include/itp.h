@@ -1,0 +1,171 @@
+/*
+ * itp.h -- C ABI of the GB300 multi-product imaginary-time propagation
+ * library (libitp.so).
+ *
+ * Method: Chin, Janecek, Krotscheck, "Any order imaginary time propagation
+ * method for solving the Schroedinger equation".  The lowest n eigenstates
+ * of H = -(1/2) nabla^2 + V (Eq. 2, Hartree units, hbar = m = 1) on a
+ * periodic 3D grid are found by repeating
+ *     phi_j = T_2k(tau) psi_j            for every state        (Eq. 3)
+ *     psi   = orthonormalised phi                                (Eq. 4)
+ * with the order-2k multi-product propagator (Eqs. mcomp, coef)
+ *     T_2k(tau) = sum_{i=1..k} c_i T_2(tau/i)^i,
+ *     c_i = prod_{j != i} i^2 / (i^2 - j^2),
+ *     T_2(tau) = exp(-tau V/2) exp(-tau T) exp(-tau V/2)         (Eq. so).
+ * tau > 0 is the imaginary time step (the paper's eps = -tau).
+ *
+ * Conventions shared by every entry point:
+ *  - Grid: nx*ny*nz points, each edge even and a product of two factors
+ *    from {1,2,3,4,6,8,12,16} (2..256 points); box [-L/2, L/2) per axis,
+ *    x_i = -L/2 + i*L/n; periodic.  Point index (z*ny + y)*nx + x.
+ *  - States: a block of m = n_states + n_guard real states, row-major
+ *    [m][nz][ny][nx] doubles on the host.  Guard states are propagated and
+ *    orthonormalised like the others; they speed up the convergence of the
+ *    highest wanted states and are reported after them.
+ *  - Normalisation: sum_r psi(r)^2 dV = 1, dV = (lx/nx)(ly/ny)(lz/nz).
+ *  - Ownership: the library owns all device memory of a handle.  Host arrays
+ *    passed in are copied during the call and may be reused on return.
+ *  - Streams: all device work of a handle is issued on the CUDA stream given
+ *    at creation (NULL = legacy default stream), in call order.  Calls that
+ *    return host data (itp_energies, itp_get_states, itp_polish,
+ *    itp_synchronize) synchronise that stream; the others do not.
+ *  - Errors: every int-returning call returns ITP_OK (0) or an ITP_ERR_*
+ *    code; itp_last_error() gives a one-line description of the most recent
+ *    failure on the handle.  A failed call leaves the states unspecified but
+ *    the handle usable (except after ITP_ERR_CUDA from a sticky device
+ *    error).
+ *  - A handle may be used by one host thread at a time.
+ */
+#ifndef ITP_H_
+#define ITP_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ITP_OK 0
+#define ITP_ERR_ARG 1      /* bad argument or unsupported size             */
+#define ITP_ERR_CUDA 2     /* a CUDA runtime call or kernel launch failed  */
+#define ITP_ERR_NOT_PD 3   /* overlap matrix not positive definite (Eq. 4) */
+#define ITP_ERR_TIMEOUT 4  /* a bounded device-side wait expired           */
+#define ITP_ERR_OOM 5      /* device memory allocation failed              */
+#define ITP_ERR_STATE 6    /* call out of order (e.g. no potential set)    */
+#define ITP_ERR_NOCONV 7   /* subspace eigen-decomposition did not converge */
+
+typedef enum {
+  ITP_FP64 = 0,  /* every step in FP64                                      */
+  ITP_MIXED = 1  /* FP32 FFT passes, FP64 combination / Cholesky / energies */
+} itp_precision;
+
+#define ITP_RITZ 1  /* itp_energies flag: Rayleigh-Ritz rotation of the states */
+
+typedef struct itp_grid* itp_handle;
+
+/* Create a handle for one problem.
+ *   out          receives the handle (NULL on failure)
+ *   nx, ny, nz   grid points per axis (see conventions)
+ *   lx, ly, lz   box lengths (bohr), > 0
+ *   n_states     wanted states n >= 1; n_guard >= 0 extra guard states;
+ *                m = n + n_guard <= 128
+ *   precision    ITP_FP64 or ITP_MIXED
+ *   cuda_stream  cudaStream_t to issue work on (NULL: default stream)
+ * Allocates all device memory for the states, the half-spectrum workspace
+ * and the FP64 accumulator.  Returns ITP_ERR_ARG / ITP_ERR_OOM /
+ * ITP_ERR_CUDA on failure. */
+int itp_create_grid(itp_handle* out, int nx, int ny, int nz, double lx, double ly, double lz,
+                    int n_states, int n_guard, int precision, void* cuda_stream);
+
+/* Release every resource of the handle (NULL is a no-op). */
+void itp_destroy(itp_handle h);
+
+/* Copy the potential V(r) (Hartree), host [nz][ny][nx] doubles.  Must be
+ * called before itp_propagate / itp_energies. */
+int itp_set_potential(itp_handle h, const double* V_host);
+
+/* Copy m = n_states + n_guard states, host [m][nz][ny][nx] doubles.  They
+ * need not be orthonormal.  ITP_MIXED rounds them to FP32. */
+int itp_set_states(itp_handle h, const double* psi_host);
+
+/* Same, from device memory (FP64, [m][N], on the handle's device; read on
+ * the handle's stream). */
+int itp_set_states_device(itp_handle h, const double* psi_device);
+
+/* Copy the current m states to host [m][nz][ny][nx] doubles (synchronises). */
+int itp_get_states(itp_handle h, double* psi_host);
+
+/* Eq. (3): phi_j = T_2k(tau) psi_j for all m states, order = 2k with
+ * 2 <= order <= 12 even, tau > 0.  The result is held in the FP64
+ * accumulator until itp_orthonormalize.  Sec. II, Eqs. (so), (mcomp),
+ * (coef): per term i the plane and pencil passes apply
+ * exp(-tau V/2i), then (FFT, exp(-tau|k|^2/2i), inverse FFT, exp(-tau V/i))
+ * i-1 times, then (FFT, kinetic, inverse FFT, exp(-tau V/2i)), and add
+ * c_i times the result; negative c_i subtract (end of Sec. II). */
+int itp_propagate(itp_handle h, int order, double tau);
+
+/* Copy the result of the last itp_propagate, phi_j = T_2k(tau) psi_j, to host
+ * [m][nz][ny][nx] doubles (synchronises).  ITP_ERR_STATE if no propagated
+ * block is pending (itp_orthonormalize consumes it). */
+int itp_get_phi(itp_handle h, double* phi_host);
+
+/* Eq. (4): S = Phi Phi^T dV, S = L L^T (FP64 Cholesky), psi = L^{-1} phi.
+ * A non-positive pivot is recorded on the device and reported as
+ * ITP_ERR_NOT_PD by the next synchronising call (itp_energies,
+ * itp_get_states, itp_synchronize). */
+int itp_orthonormalize(itp_handle h);
+
+/* Energies of the (orthonormal) current states, FP64 (Eq. 2):
+ *   E_host[j], j < m, receives (psi_j|H|psi_j) dV, or with flags & ITP_RITZ
+ *   the eigenvalues (ascending) of the subspace matrix (psi_i|H|psi_j) dV,
+ *   and the states are rotated onto its eigenvectors (the subspace step of
+ *   Sec. III).  E_host may be NULL.  Synchronises; returns a pending
+ *   ITP_ERR_NOT_PD / ITP_ERR_NOCONV. */
+int itp_energies(itp_handle h, double* E_host, int flags);
+
+/* Mixed precision only: switch the states to FP64 and iterate FP64 steps
+ * (propagate, orthonormalise, Ritz energies) until
+ * max_{j<n_states} |E_j - E_j(previous)| < tol or max_steps steps.
+ * steps_out (nullable) receives the number of steps, E_host (nullable) the
+ * m final energies.  Later itp_propagate calls continue in FP32. */
+int itp_polish(itp_handle h, int order, double tau, double tol, int max_steps, int* steps_out,
+               double* E_host);
+
+/* Wait for the handle's stream; returns a pending device status. */
+int itp_synchronize(itp_handle h);
+
+/* One-line description of the last error on the handle ("" if none); with
+ * h == NULL, the reason the calling thread's last itp_create_grid failed
+ * (a failed create returns no handle). */
+const char* itp_last_error(itp_handle h);
+
+/* Number of device kernels the handle has launched so far. */
+long long itp_kernel_launches(itp_handle h);
+
+/* Kernel kinds for per-kernel timing. */
+#define ITP_KERNEL_PLANE_FWD 0        /* real state -> half spectrum (plane pass)    */
+#define ITP_KERNEL_PLANE_MERGED 1     /* inverse, exp(-tau V/i), forward (plane pass) */
+#define ITP_KERNEL_PLANE_COMBINE 2    /* inverse, exp(-tau V/2i), FP64 c_i sum        */
+#define ITP_KERNEL_PLANE_HPSI 3       /* inverse, + V psi (H psi for the energies)    */
+#define ITP_KERNEL_PENCIL 4           /* z FFT, exp(-tau|k|^2/2i), inverse z FFT      */
+#define ITP_KERNEL_PENCIL_KINETIC 5   /* z FFT, |k|^2/2, inverse z FFT                */
+#define ITP_KERNEL_GRAM 6             /* overlap / subspace Gram partial sums         */
+#define ITP_KERNEL_GRAM_REDUCE 7
+#define ITP_KERNEL_CHOLESKY 8
+#define ITP_KERNEL_EIGH 9
+#define ITP_KERNEL_APPLY 10           /* n x n matrix applied to the state block      */
+#define ITP_KERNEL_OTHER 11           /* tables, conversions, diagonal                */
+#define ITP_KERNEL_KINDS 12
+
+/* Per-kernel timing: with enable != 0 every later launch is bracketed by
+ * CUDA events on the handle's stream (a few microseconds of overhead per
+ * launch); calling it again clears the record.  Synchronises. */
+int itp_profile(itp_handle h, int enable);
+
+/* Launch count and summed device time (ms) of one ITP_KERNEL_* kind since
+ * the last itp_profile call.  Synchronises. */
+int itp_profile_read(itp_handle h, int kind, long long* launches, double* total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ITP_H_ */

@@ -22,7 +22,10 @@ the Gaussian C60-like well stands in for it):
 """
 from __future__ import annotations
 
+import ctypes
 import math
+import os
+import subprocess
 from dataclasses import dataclass
 
 import numpy as np
@@ -80,25 +83,60 @@ def uniform53(hi, lo):
 
 _TAG_STATES = 0x5157A7E5  # stream tag of the initial-state draws
 
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_NATIVE = os.path.join(_HERE, "libphilox.so")
+_native_lib = None
+
+
+def build_native() -> str:
+    """Compile philox.c (the same generator in C, for large inputs)."""
+    src = os.path.join(_HERE, "philox.c")
+    if not os.path.exists(_NATIVE) or os.path.getmtime(_NATIVE) < os.path.getmtime(src):
+        subprocess.run(["gcc", "-O2", "-shared", "-fPIC", "-o", _NATIVE + ".tmp", src],
+                       check=True)
+        os.replace(_NATIVE + ".tmp", _NATIVE)
+    return _NATIVE
+
+
+def _native():
+    global _native_lib
+    if _native_lib is None and os.path.exists(_NATIVE):
+        lib = ctypes.CDLL(_NATIVE)
+        lib.philox_uniform_pairs.restype = None
+        lib.philox_uniform_pairs.argtypes = [ctypes.c_uint64] + [ctypes.c_uint32] * 6 + [
+            ctypes.c_void_p]
+        _native_lib = lib
+    return _native_lib
+
+
+def _state_uniforms(npairs, state, problem, k0, k1, use_native=True):
+    """(u1, u2) of the Philox draws (pair, state, problem, states tag)."""
+    lib = _native() if use_native else None
+    if lib is not None:
+        u = np.empty(2 * npairs)
+        lib.philox_uniform_pairs(npairs, 0, state & _U32, problem & _U32, _TAG_STATES, k0, k1,
+                                 u.ctypes.data)
+        return u[0::2], u[1::2]
+    pairs = np.arange(npairs, dtype=np.uint32)
+    r0, r1, r2, r3 = philox4x32_10(pairs, state, problem, _TAG_STATES, k0, k1)
+    return uniform53(r0, r1), uniform53(r2, r3)
+
 
 def normal_states(n_states: int, n_points: int, seed: int, problem: int = 0,
-                  first_state: int = 0) -> np.ndarray:
+                  first_state: int = 0, use_native: bool = True) -> np.ndarray:
     """Random-normal initial states, shape (n_states, n_points), float64.
 
     State j (global index first_state + j), point p takes the Box-Muller
     normal number (p % 2) of the Philox draw at counter
-    (p // 2, j, problem, tag) under key (seed, seed >> 32).
+    (p // 2, j, problem, tag) under key (seed, seed >> 32).  The C and numpy
+    Philox give identical uniforms; the Box-Muller step is numpy in both.
     """
     if n_points % 2:
         raise ValueError("n_points must be even")
     out = np.empty((n_states, n_points), dtype=np.float64)
-    pairs = np.arange(n_points // 2, dtype=np.uint32)
     k0, k1 = int(seed) & _U32, (int(seed) >> 32) & _U32
     for j in range(n_states):
-        r0, r1, r2, r3 = philox4x32_10(pairs, first_state + j, problem,
-                                       _TAG_STATES, k0, k1)
-        u1 = uniform53(r0, r1)
-        u2 = uniform53(r2, r3)
+        u1, u2 = _state_uniforms(n_points // 2, first_state + j, problem, k0, k1, use_native)
         rad = np.sqrt(-2.0 * np.log(u1))
         ang = 2.0 * np.pi * u2
         out[j, 0::2] = rad * np.cos(ang)

@@ -1,0 +1,429 @@
+// Dense n x n side of one iteration (Eq. 4 and the subspace step of
+// Sec. III): Gram sums over the grid, Cholesky + triangular inverse, the
+// symmetric eigen-decomposition, and the application of an n x n matrix to
+// the block of states.  These are the CUDA-core versions; all small-matrix
+// work is FP64.
+#include <math.h>
+
+#include "itp_kernels.cuh"
+
+namespace itp {
+
+namespace {
+
+constexpr int kMaxM = 128;
+
+// ---------------------------------------------------------------------------
+// Gram partial sums over chunks of points.  512 threads as 16 (tx) x 32 (ty);
+// thread owns rows i = ty + 32*q (q < 4) and cols j = tx + 16*r (r < 8).
+// points per shared tile: 32 (FP32) or 16 (FP64), 33 KB of shared tiles;
+// FP32 products are summed over runs of 256 points, then in FP64.
+template <typename TC> struct GramTile { static constexpr int KT = sizeof(TC) == 4 ? 32 : 16; };
+constexpr int kGramRun = 256;
+
+template <typename TA, typename TB, typename TC>
+__global__ void __launch_bounds__(512) gram_partial_kernel(const TA* __restrict__ A,
+                                                           const TB* __restrict__ B, int m,
+                                                           long long N, long long chunk,
+                                                           double* __restrict__ partial) {
+  constexpr int KT = GramTile<TC>::KT;
+  constexpr int kFlushTiles = kGramRun / KT;
+  __shared__ TC sA[KT][kMaxM + 1];
+  __shared__ TC sB[KT][kMaxM + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const long long p_begin = (long long)blockIdx.x * chunk;
+  const long long p_end = min(N, p_begin + chunk);
+  double accd[4][8];
+  TC accf[4][8];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int r = 0; r < 8; ++r) { accd[q][r] = 0.0; accf[q][r] = (TC)0; }
+  int tiles_in_run = 0;
+  for (long long p0 = p_begin; p0 < p_end; p0 += KT) {
+    // load tiles: element (row i, point p0 + k)
+    for (int e = threadIdx.x; e < KT * kMaxM; e += blockDim.x) {
+      const int i = e / KT, k = e - i * KT;
+      const long long p = p0 + k;
+      TC va = (TC)0, vb = (TC)0;
+      if (i < m && p < p_end) {
+        va = (TC)A[(long long)i * N + p];
+        vb = (TC)B[(long long)i * N + p];
+      }
+      sA[k][i] = va;
+      sB[k][i] = vb;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < KT; ++k) {
+      TC a[4], b[8];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) a[q] = sA[k][ty + 32 * q];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) b[r] = sB[k][tx + 16 * r];
+      if constexpr (sizeof(TC) == 8) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int r = 0; r < 8; ++r) accd[q][r] = fma((double)a[q], (double)b[r], accd[q][r]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int r = 0; r < 8; ++r) accf[q][r] = fma(a[q], b[r], accf[q][r]);
+      }
+    }
+    __syncthreads();
+    if (sizeof(TC) == 4 && ++tiles_in_run == kFlushTiles) {
+      tiles_in_run = 0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) { accd[q][r] += (double)accf[q][r]; accf[q][r] = (TC)0; }
+    }
+  }
+  double* out = partial + (long long)blockIdx.x * m * m;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = ty + 32 * q;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int j = tx + 16 * r;
+      if (i < m && j < m) out[i * m + j] = accd[q][r] + (double)accf[q][r];
+    }
+  }
+}
+
+__global__ void gram_reduce_kernel(const double* __restrict__ partial, int n_chunks, int m,
+                                   double scale, int sym, double* __restrict__ G) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * m) return;
+  const int i = e / m, j = e - i * m;
+  double s = 0.0, t = 0.0;
+  for (int c = 0; c < n_chunks; ++c) {
+    s += partial[(long long)c * m * m + i * m + j];
+    if (sym) t += partial[(long long)c * m * m + j * m + i];
+  }
+  G[e] = sym ? 0.5 * scale * (s + t) : scale * s;
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky (right-looking, column by column) and the lower-triangular
+// inverse by forward substitution, one CTA, matrix in shared memory.
+__global__ void __launch_bounds__(1024) cholesky_inverse_kernel(const double* __restrict__ S,
+                                                                int m, double* __restrict__ Minv,
+                                                                int* status) {
+  extern __shared__ double sh[];
+  const int P = m + 1;
+  double* L = sh;              // m x P
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e - i * m;
+    L[i * P + j] = S[e];
+  }
+  __syncthreads();
+  for (int k = 0; k < m; ++k) {
+    if (threadIdx.x == 0) {
+      const double d = L[k * P + k];
+      if (!(d > 0.0) || !isfinite(d)) {
+        bad = 1;
+        L[k * P + k] = 1.0;
+      } else {
+        L[k * P + k] = sqrt(d);
+      }
+    }
+    __syncthreads();
+    const double piv = L[k * P + k];
+    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) L[i * P + k] /= piv;
+    __syncthreads();
+    const int rem = m - k - 1;
+    for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+      const int i = k + 1 + e / rem, j = k + 1 + e % rem;
+      if (j <= i) L[i * P + j] -= L[i * P + k] * L[j * P + k];
+    }
+    __syncthreads();
+  }
+  // Minv = L^{-1}: column j solves L x = e_j by forward substitution; each
+  // thread owns one column of the output in global memory.
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    for (int i = 0; i < j; ++i) Minv[i * m + j] = 0.0;
+    Minv[j * m + j] = 1.0 / L[j * P + j];
+    for (int i = j + 1; i < m; ++i) {
+      double s = 0.0;
+      for (int k = j; k < i; ++k) s = fma(L[i * P + k], Minv[k * m + j], s);
+      Minv[i * m + j] = -s / L[i * P + i];
+    }
+  }
+  if (threadIdx.x == 0 && bad) atomicOr(status, 1);
+}
+
+// ---------------------------------------------------------------------------
+// Parallel cyclic Jacobi (round-robin pairing: m/2 disjoint rotations per
+// round, m-1 rounds per sweep).  A in shared memory (pitch m+1), U^T in
+// global memory (row p of U^T is eigenvector p).
+__global__ void __launch_bounds__(1024) jacobi_kernel(const double* __restrict__ H, int m,
+                                                      double* __restrict__ E,
+                                                      double* __restrict__ Rt,
+                                                      double* __restrict__ Ut, int* status) {
+  extern __shared__ double sh[];
+  const int mm = (m + 1) & ~1;          // even number of players (a dummy if m is odd)
+  const int P = m + 1;
+  double* A = sh;                        // m x P
+  double* cs = sh + m * P;               // [mm/2] c, [mm/2] s
+  int* pr = reinterpret_cast<int*>(cs + mm);   // [mm/2] p, [mm/2] q
+  __shared__ double off_norm, tot_norm;
+  __shared__ int done;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int e = tid; e < m * m; e += nthr) {
+    const int i = e / m, j = e - i * m;
+    A[i * P + j] = 0.5 * (H[i * m + j] + H[j * m + i]);
+    Ut[e] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int npairs = mm / 2;
+  int sweep;
+  for (sweep = 0; sweep < 40; ++sweep) {
+    if (tid == 0) { off_norm = 0.0; tot_norm = 0.0; }
+    __syncthreads();
+    double lo = 0.0, lt = 0.0;
+    for (int e = tid; e < m * m; e += nthr) {
+      const int i = e / m, j = e - i * m;
+      const double v = A[i * P + j] * A[i * P + j];
+      lt += v;
+      if (i != j) lo += v;
+    }
+    atomicAdd(&off_norm, lo);
+    atomicAdd(&tot_norm, lt);
+    __syncthreads();
+    // off-diagonal Frobenius norm <= 1e-13 of the total: eigenvalue errors
+    // are then second order in it (~1e-26 |H|^2 / gap)
+    if (tid == 0) done = (off_norm <= 1e-26 * tot_norm) || (off_norm == 0.0);
+    __syncthreads();
+    if (done) break;
+    for (int round = 0; round < mm - 1; ++round) {
+      for (int t = tid; t < npairs; t += nthr) {
+        // players 0..mm-1; player 0 fixed, the others rotate
+        const int a = (t == 0) ? 0 : 1 + (t - 1 + round) % (mm - 1);
+        const int b = 1 + (mm - 2 - t + round) % (mm - 1);
+        int p = min(a, b), q = max(a, b);
+        double c = 1.0, s = 0.0;
+        if (q < m) {
+          const double apq = A[p * P + q];
+          if (apq != 0.0) {
+            const double app = A[p * P + p], aqq = A[q * P + q];
+            const double zeta = (aqq - app) / (2.0 * apq);
+            const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            c = 1.0 / sqrt(1.0 + tt * tt);
+            s = tt * c;
+          }
+        } else {
+          p = q = -1;
+        }
+        cs[t] = c;
+        cs[npairs + t] = s;
+        pr[t] = p;
+        pr[npairs + t] = q;
+      }
+      __syncthreads();
+      // columns: A <- A J
+      for (int e = tid; e < npairs * m; e += nthr) {
+        const int t = e / m, r = e - t * m;
+        const int p = pr[t], q = pr[npairs + t];
+        if (p < 0) continue;
+        const double c = cs[t], s = cs[npairs + t];
+        const double arp = A[r * P + p], arq = A[r * P + q];
+        A[r * P + p] = c * arp - s * arq;
+        A[r * P + q] = s * arp + c * arq;
+      }
+      __syncthreads();
+      // rows: A <- J^T A ; and U^T <- J^T U^T (rows p, q)
+      for (int e = tid; e < npairs * m; e += nthr) {
+        const int t = e / m, r = e - t * m;
+        const int p = pr[t], q = pr[npairs + t];
+        if (p < 0) continue;
+        const double c = cs[t], s = cs[npairs + t];
+        const double apr = A[p * P + r], aqr = A[q * P + r];
+        A[p * P + r] = c * apr - s * aqr;
+        A[q * P + r] = s * apr + c * aqr;
+        const double up = Ut[p * m + r], uq = Ut[q * m + r];
+        Ut[p * m + r] = c * up - s * uq;
+        Ut[q * m + r] = s * up + c * uq;
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0 && sweep >= 40) atomicOr(status, 2);
+  __syncthreads();
+  // sort eigenvalues ascending (stable by index) and permute the rows of U^T
+  for (int i = tid; i < m; i += nthr) {
+    const double ei = A[i * P + i];
+    int rank = 0;
+    for (int j = 0; j < m; ++j) {
+      const double ej = A[j * P + j];
+      rank += (ej < ei) || (ej == ei && j < i);
+    }
+    E[rank] = ei;
+    for (int r = 0; r < m; ++r) Rt[rank * m + r] = Ut[i * m + r];
+  }
+}
+
+__global__ void diag_kernel(const double* __restrict__ H, int m, double* __restrict__ E) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) E[i] = H[i * m + i];
+}
+
+// ---------------------------------------------------------------------------
+// Y = M X.  Persistent CTAs over tiles of 32 points; M (as TC) stays in
+// shared memory.  512 threads: tx = point in tile, ty = row group (16 rows).
+constexpr int kApplyPT = 32;
+
+template <typename TX, typename TY, typename TC>
+__global__ void __launch_bounds__(512) apply_matrix_kernel(const double* __restrict__ M, int m,
+                                                           int lower, const TX* __restrict__ X,
+                                                           TY* __restrict__ Y, long long N) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TC* sM = reinterpret_cast<TC*>(smraw);            // m x m
+  TC* sX = sM + m * m;                              // m x kApplyPT
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // ty in 0..15
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) sM[e] = (TC)M[e];
+  const long long ntiles = (N + kApplyPT - 1) / kApplyPT;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long p0 = tile * kApplyPT;
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * kApplyPT; e += blockDim.x) {
+      const int k = e / kApplyPT, j = e - k * kApplyPT;
+      const long long p = p0 + j;
+      sX[e] = (p < N) ? (TC)X[(long long)k * N + p] : (TC)0;
+    }
+    __syncthreads();
+    const long long p = p0 + tx;
+    for (int i0 = ty; i0 < m; i0 += 16 * 8) {
+      TC acc[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] = (TC)0;
+      const int kmax = lower ? min(m, i0 + 16 * 7 + 1) : m;
+      for (int k = 0; k < kmax; ++k) {
+        const TC x = sX[k * kApplyPT + tx];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int i = i0 + 16 * q;
+          if (i < m) acc[q] = fma(sM[i * m + k], x, acc[q]);
+        }
+      }
+      if (p < N) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int i = i0 + 16 * q;
+          if (i < m) Y[(long long)i * N + p] = (TY)acc[q];
+        }
+      }
+    }
+  }
+}
+
+template <typename TS, typename TD>
+__global__ void convert_kernel(const TS* __restrict__ src, TD* __restrict__ dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (TD)src[i];
+}
+
+template <typename T> struct ComputeOf;
+template <> struct ComputeOf<float> { using type = float; };
+template <> struct ComputeOf<double> { using type = double; };
+
+}  // namespace
+
+template <typename TA, typename TB, typename TC>
+cudaError_t launch_gram_partial(const TA* A, const TB* B, int m, long long n_points, int n_chunks,
+                                double* partial, cudaStream_t st) {
+  if (m > kMaxM) return cudaErrorInvalidValue;
+  long long chunk = (n_points + n_chunks - 1) / n_chunks;
+  chunk = (chunk + kGramRun - 1) / kGramRun * kGramRun;
+  gram_partial_kernel<TA, TB, TC><<<n_chunks, 512, 0, st>>>(A, B, m, n_points, chunk, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_reduce(const double* partial, int n_chunks, int m, double scale, int sym,
+                               double* G, cudaStream_t st) {
+  gram_reduce_kernel<<<(m * m + 255) / 256, 256, 0, st>>>(partial, n_chunks, m, scale, sym, G);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cholesky_inverse(const double* S, int m, double* Minv, int* status,
+                                    cudaStream_t st) {
+  if (m > kMaxM) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)m * (m + 1) * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(cholesky_inverse_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cholesky_inverse_kernel<<<1, 1024, smem, st>>>(S, m, Minv, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jacobi_eigh(const double* H, int m, double* E, double* Rt, double* work,
+                               int* status, cudaStream_t st) {
+  if (m > kMaxM) return cudaErrorInvalidValue;
+  const int mm = (m + 1) & ~1;
+  const size_t smem = (size_t)m * (m + 1) * sizeof(double) + (size_t)mm * sizeof(double) +
+                      (size_t)mm * sizeof(int);
+  cudaError_t e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  jacobi_kernel<<<1, 1024, smem, st>>>(H, m, E, Rt, work, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag(const double* H, int m, double* E, cudaStream_t st) {
+  diag_kernel<<<1, 128, 0, st>>>(H, m, E);
+  return cudaGetLastError();
+}
+
+template <typename TX, typename TY>
+cudaError_t launch_apply_matrix(const double* M, int m, int lower, const TX* X, TY* Y,
+                                long long n_points, cudaStream_t st) {
+  using TC = typename ComputeOf<TY>::type;
+  if (m > kMaxM) return cudaErrorInvalidValue;
+  const size_t smem = ((size_t)m * m + (size_t)m * kApplyPT) * sizeof(TC);
+  cudaError_t e = cudaFuncSetAttribute(apply_matrix_kernel<TX, TY, TC>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long ntiles = (n_points + kApplyPT - 1) / kApplyPT;
+  const long long cap = (long long)sms * (smem > 110000 ? 1 : 2);
+  const int blocks = (int)(ntiles < cap ? ntiles : cap);
+  apply_matrix_kernel<TX, TY, TC><<<blocks, 512, smem, st>>>(M, m, lower, X, Y, n_points);
+  return cudaGetLastError();
+}
+
+template <typename TS, typename TD>
+cudaError_t launch_convert(const TS* src, TD* dst, long long count, cudaStream_t st) {
+  convert_kernel<TS, TD><<<4 * 152, 256, 0, st>>>(src, dst, count);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_gram_partial<double, double, double>(const double*, const double*, int,
+                                                                 long long, int, double*,
+                                                                 cudaStream_t);
+template cudaError_t launch_gram_partial<double, double, float>(const double*, const double*, int,
+                                                                long long, int, double*,
+                                                                cudaStream_t);
+template cudaError_t launch_gram_partial<float, double, float>(const float*, const double*, int,
+                                                               long long, int, double*,
+                                                               cudaStream_t);
+template cudaError_t launch_gram_partial<float, double, double>(const float*, const double*, int,
+                                                                long long, int, double*,
+                                                                cudaStream_t);
+template cudaError_t launch_apply_matrix<double, double>(const double*, int, int, const double*,
+                                                         double*, long long, cudaStream_t);
+template cudaError_t launch_apply_matrix<double, float>(const double*, int, int, const double*,
+                                                        float*, long long, cudaStream_t);
+template cudaError_t launch_apply_matrix<float, float>(const double*, int, int, const float*,
+                                                       float*, long long, cudaStream_t);
+template cudaError_t launch_convert<float, double>(const float*, double*, long long, cudaStream_t);
+template cudaError_t launch_convert<double, float>(const double*, float*, long long, cudaStream_t);
+
+}  // namespace itp

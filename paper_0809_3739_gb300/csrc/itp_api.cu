@@ -1,0 +1,731 @@
+// C ABI of libitp (declared in include/itp.h): handle management and the
+// orchestration of the plane / pencil passes and the dense kernels that make
+// up one imaginary-time iteration (Eqs. 3 and 4 of the paper).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "itp.h"
+#include "itp_kernels.cuh"
+
+using namespace itp;
+
+namespace {
+
+constexpr int kMaxStates = 128;
+constexpr int kMaxTerms = 6;   // order <= 12
+constexpr size_t kSmemLimit = 227 * 1024;
+
+template <typename R>
+struct Lane {
+  bool ready = false;
+  R* psi = nullptr;          // [m][N]
+  R* psi_tmp = nullptr;      // [m][N]
+  void* work = nullptr;      // [m][n_half] complex
+  R* f_half[kMaxTerms] = {}; // exp(-tau_i V / 2)
+  R* f_full[kMaxTerms] = {}; // exp(-tau_i V)      (terms i >= 2)
+  R* ktab = nullptr;         // per term: nxh + ny + nz propagation factors
+  R* htab = nullptr;         // nxh + ny + nz kinetic values k^2/2
+  void* twx = nullptr;
+  void* twy = nullptr;
+  void* twz = nullptr;
+  int tab_order = 0;
+  double tab_tau = 0.0;
+};
+
+}  // namespace
+
+struct itp_grid {
+  int device = 0;
+  GridDesc g{};
+  double lx = 0, ly = 0, lz = 0, dV = 0;
+  int n = 0, ng = 0, m = 0;
+  int precision = ITP_FP64;
+  cudaStream_t st = nullptr;
+  double* V = nullptr;        // [N]
+  double* acc = nullptr;      // [m][N] FP64 accumulator / H psi / staging
+  Lane<float> f32;
+  Lane<double> f64;
+  bool cur64 = true;          // which lane holds the states
+  bool have_V = false, have_states = false, have_phi = false;
+  int n_chunks = 0;
+  double* partial = nullptr;  // [n_chunks][m][m]
+  double* S = nullptr;        // [m][m]
+  double* Mx = nullptr;       // [m][m]
+  double* Hs = nullptr;       // [m][m]
+  double* Wmm = nullptr;      // [m][m]
+  double* E_dev = nullptr;    // [m]
+  int* status = nullptr;      // device status word
+  int* status_host = nullptr; // pinned
+  double* E_host_pinned = nullptr;
+  long long launches = 0;
+  std::string err;
+  // optional per-kernel event timing (itp_profile)
+  bool prof = false;
+  struct ProfEvent { int kind; cudaEvent_t start, stop; };
+  std::vector<ProfEvent> prof_events;
+  size_t prof_used = 0;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(itp_handle h, int code, const char* fmt, ...) {
+  if (h) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    h->err = buf;
+  }
+  return code;
+}
+
+#define ITP_CUDA(h, expr)                                                                 \
+  do {                                                                                    \
+    cudaError_t e_ = (expr);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(h, e_ == cudaErrorMemoryAllocation ? ITP_ERR_OOM : ITP_ERR_CUDA,        \
+                  "%s: %s", #expr, cudaGetErrorString(e_));                               \
+  } while (0)
+
+// Launch one kernel of the given ITP_KERNEL_* kind, counted and (when
+// profiling is on) bracketed by CUDA events on the handle's stream.
+#define ITP_LAUNCH(h, kind, expr)                                                         \
+  do {                                                                                    \
+    (h)->launches++;                                                                      \
+    const long ev_ = prof_begin(h, kind);                                                 \
+    cudaError_t e_ = (expr);                                                              \
+    prof_end(h, ev_);                                                                     \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(h, ITP_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_));              \
+  } while (0)
+
+long prof_begin(itp_handle h, int kind) {
+  if (!h->prof) return -1;
+  if (h->prof_used == h->prof_events.size()) {
+    itp_grid::ProfEvent e{kind, nullptr, nullptr};
+    if (cudaEventCreate(&e.start) != cudaSuccess || cudaEventCreate(&e.stop) != cudaSuccess)
+      return -1;
+    h->prof_events.push_back(e);
+  }
+  itp_grid::ProfEvent& e = h->prof_events[h->prof_used];
+  e.kind = kind;
+  if (cudaEventRecord(e.start, h->st) != cudaSuccess) return -1;
+  return (long)h->prof_used++;
+}
+
+void prof_end(itp_handle h, long idx) {
+  if (idx >= 0) cudaEventRecord(h->prof_events[idx].stop, h->st);
+}
+
+#define ITP_TRY(expr)             \
+  do {                            \
+    int r_ = (expr);              \
+    if (r_ != ITP_OK) return r_;  \
+  } while (0)
+
+bool split_axis(int L, int* r1, int* r2) {
+  static const int rad[] = {2, 3, 4, 6, 8, 12, 16};
+  if (L < 2 || L > 256 || (L & 1)) return false;
+  if (L <= 16) {
+    for (int r : rad)
+      if (r == L) { *r1 = 1; *r2 = L; return true; }
+  }
+  int best = -1;
+  for (int a : rad) {
+    if (L % a) continue;
+    const int b = L / a;
+    bool ok = false;
+    for (int r : rad) ok |= (r == b);
+    if (!ok || b < a) continue;   // r2 >= r1
+    if (best < 0 || (b - a) < (L / best - best)) best = a;
+  }
+  if (best < 0) return false;
+  *r1 = best;
+  *r2 = L / best;
+  return true;
+}
+
+// Exact c_i of Eq. (coef) as a reduced fraction, then rounded to double.
+double mp_coefficient(int i, int k) {
+  long long num = 1, den = 1;
+  auto gcd = [](long long a, long long b) {
+    a = a < 0 ? -a : a;
+    b = b < 0 ? -b : b;
+    while (b) { long long t = a % b; a = b; b = t; }
+    return a;
+  };
+  for (int j = 1; j <= k; ++j) {
+    if (j == i) continue;
+    long long a = (long long)i * i, b = (long long)i * i - (long long)j * j;
+    num *= a;
+    den *= b;
+    const long long gg = gcd(num, den);
+    num /= gg;
+    den /= gg;
+  }
+  return (double)num / (double)den;
+}
+
+template <typename R>
+void roots_table(int L, std::vector<R>& out) {
+  out.resize(2 * (size_t)L);
+  for (int j = 0; j < L; ++j) {
+    double c, s;
+    if ((4 * j) % L == 0) {   // quarter turns exactly
+      const int q = (4 * j) / L;
+      c = (q == 0) ? 1.0 : (q == 2 ? -1.0 : 0.0);
+      s = (q == 1) ? -1.0 : (q == 3 ? 1.0 : 0.0);
+    } else {
+      const double ang = 2.0 * 3.14159265358979323846 * (double)j / (double)L;
+      c = std::cos(ang);
+      s = -std::sin(ang);
+    }
+    out[2 * j] = (R)c;
+    out[2 * j + 1] = (R)s;
+  }
+}
+
+template <typename R>
+int alloc_lane(itp_handle h, Lane<R>& L) {
+  if (L.ready) return ITP_OK;
+  const GridDesc& g = h->g;
+  const size_t N = (size_t)g.n_points, Nh = (size_t)g.n_half, m = (size_t)h->m;
+  ITP_CUDA(h, cudaMalloc(&L.psi, m * N * sizeof(R)));
+  ITP_CUDA(h, cudaMalloc(&L.psi_tmp, m * N * sizeof(R)));
+  ITP_CUDA(h, cudaMalloc(&L.work, m * Nh * 2 * sizeof(R)));
+  for (int i = 0; i < kMaxTerms; ++i) {
+    ITP_CUDA(h, cudaMalloc(&L.f_half[i], N * sizeof(R)));
+    if (i > 0) ITP_CUDA(h, cudaMalloc(&L.f_full[i], N * sizeof(R)));
+  }
+  const size_t tl = (size_t)g.nxh + g.ny + g.nz;
+  ITP_CUDA(h, cudaMalloc(&L.ktab, kMaxTerms * tl * sizeof(R)));
+  ITP_CUDA(h, cudaMalloc(&L.htab, tl * sizeof(R)));
+  std::vector<R> tx, ty, tz;
+  roots_table<R>(g.nx, tx);
+  roots_table<R>(g.ny, ty);
+  roots_table<R>(g.nz, tz);
+  ITP_CUDA(h, cudaMalloc(&L.twx, tx.size() * sizeof(R)));
+  ITP_CUDA(h, cudaMalloc(&L.twy, ty.size() * sizeof(R)));
+  ITP_CUDA(h, cudaMalloc(&L.twz, tz.size() * sizeof(R)));
+  ITP_CUDA(h, cudaMemcpy(L.twx, tx.data(), tx.size() * sizeof(R), cudaMemcpyHostToDevice));
+  ITP_CUDA(h, cudaMemcpy(L.twy, ty.data(), ty.size() * sizeof(R), cudaMemcpyHostToDevice));
+  ITP_CUDA(h, cudaMemcpy(L.twz, tz.data(), tz.size() * sizeof(R), cudaMemcpyHostToDevice));
+  ITP_LAUNCH(h, ITP_KERNEL_OTHER, launch_kinetic_tables<R>(g, h->lx, h->ly, h->lz, L.htab, L.htab + g.nxh,
+                                         L.htab + g.nxh + g.ny, h->st));
+  L.tab_order = 0;
+  L.ready = true;
+  return ITP_OK;
+}
+
+template <typename R>
+void free_lane(Lane<R>& L) {
+  cudaFree(L.psi);
+  cudaFree(L.psi_tmp);
+  cudaFree(L.work);
+  for (int i = 0; i < kMaxTerms; ++i) {
+    cudaFree(L.f_half[i]);
+    cudaFree(L.f_full[i]);
+  }
+  cudaFree(L.ktab);
+  cudaFree(L.htab);
+  cudaFree(L.twx);
+  cudaFree(L.twy);
+  cudaFree(L.twz);
+  L = Lane<R>();
+}
+
+template <typename R>
+Lane<R>& lane_of(itp_handle h);
+template <>
+Lane<float>& lane_of<float>(itp_handle h) { return h->f32; }
+template <>
+Lane<double>& lane_of<double>(itp_handle h) { return h->f64; }
+
+// Per-term factor tables for (order, tau).
+template <typename R>
+int prepare_tables(itp_handle h, Lane<R>& L, int k, double tau) {
+  if (L.tab_order == 2 * k && L.tab_tau == tau) return ITP_OK;
+  const GridDesc& g = h->g;
+  const size_t tl = (size_t)g.nxh + g.ny + g.nz;
+  for (int i = 1; i <= k; ++i) {
+    R* kt = L.ktab + (i - 1) * tl;
+    ITP_LAUNCH(h, ITP_KERNEL_OTHER, launch_term_tables<R>(g, h->V, tau / i, h->lx, h->ly, h->lz, L.f_half[i - 1],
+                                        i > 1 ? L.f_full[i - 1] : nullptr, kt, kt + g.nxh,
+                                        kt + g.nxh + g.ny, h->st));
+  }
+  L.tab_order = 2 * k;
+  L.tab_tau = tau;
+  return ITP_OK;
+}
+
+// Eq. (3) with the order-2k expansion: acc = sum_i c_i T_2(tau/i)^i psi.
+template <typename R>
+int propagate_lane(itp_handle h, int k, double tau) {
+  Lane<R>& L = lane_of<R>(h);
+  ITP_TRY(prepare_tables<R>(h, L, k, tau));
+  const GridDesc& g = h->g;
+  const size_t tl = (size_t)g.nxh + g.ny + g.nz;
+  for (int i = 1; i <= k; ++i) {
+    PlaneArgs<R> pa{};
+    pa.m = h->m;
+    pa.in_real = L.psi;
+    pa.spec = L.work;
+    pa.twx = L.twx;
+    pa.twy = L.twy;
+    pa.mode = PLANE_FWD_REAL;
+    pa.f_in = L.f_half[i - 1];
+    ITP_LAUNCH(h, ITP_KERNEL_PLANE_FWD, launch_plane<R>(g, pa, h->st));
+    PencilArgs<R> pe{};
+    pe.mode = PENCIL_PROPAGATE;
+    pe.m = h->m;
+    pe.spec = L.work;
+    pe.kx_tab = L.ktab + (i - 1) * tl;
+    pe.ky_tab = pe.kx_tab + g.nxh;
+    pe.kz_tab = pe.ky_tab + g.ny;
+    pe.scale = (R)1;
+    pe.twz = L.twz;
+    for (int j = 1; j <= i; ++j) {
+      ITP_LAUNCH(h, pe.mode == PENCIL_PROPAGATE ? ITP_KERNEL_PENCIL : ITP_KERNEL_PENCIL_KINETIC,
+                 launch_pencil<R>(g, pe, h->st));
+      if (j < i) {
+        PlaneArgs<R> pm = pa;
+        pm.mode = PLANE_MERGED;
+        pm.f_in = nullptr;
+        pm.f_mid = L.f_full[i - 1];
+        ITP_LAUNCH(h, ITP_KERNEL_PLANE_MERGED, launch_plane<R>(g, pm, h->st));
+      }
+    }
+    PlaneArgs<R> pc = pa;
+    pc.mode = PLANE_COMBINE;
+    pc.f_in = nullptr;
+    pc.f_out = L.f_half[i - 1];
+    pc.acc = h->acc;
+    pc.coef = mp_coefficient(i, k);
+    pc.acc_init = (i == 1);
+    ITP_LAUNCH(h, ITP_KERNEL_PLANE_COMBINE, launch_plane<R>(g, pc, h->st));
+  }
+  return ITP_OK;
+}
+
+// Eq. (4): psi = L^{-1} phi, S = phi phi^T dV = L L^T.
+template <typename R>
+int orthonormalize_lane(itp_handle h) {
+  Lane<R>& L = lane_of<R>(h);
+  using TC = R;   // FP32 products for the mixed path, FP64 for the FP64 path
+  ITP_LAUNCH(h, ITP_KERNEL_GRAM, (launch_gram_partial<double, double, TC>(h->acc, h->acc, h->m, h->g.n_points,
+                                                         h->n_chunks, h->partial, h->st)));
+  ITP_LAUNCH(h, ITP_KERNEL_GRAM_REDUCE, launch_gram_reduce(h->partial, h->n_chunks, h->m, h->dV, 1, h->S, h->st));
+  ITP_LAUNCH(h, ITP_KERNEL_CHOLESKY, launch_cholesky_inverse(h->S, h->m, h->Mx, h->status, h->st));
+  ITP_LAUNCH(h, ITP_KERNEL_APPLY, (launch_apply_matrix<double, R>(h->Mx, h->m, 1, h->acc, L.psi, h->g.n_points,
+                                                h->st)));
+  return ITP_OK;
+}
+
+// H psi into acc, subspace matrix, optional Ritz rotation; E into E_dev.
+template <typename R>
+int energies_lane(itp_handle h, int flags) {
+  Lane<R>& L = lane_of<R>(h);
+  const GridDesc& g = h->g;
+  PlaneArgs<R> pa{};
+  pa.m = h->m;
+  pa.in_real = L.psi;
+  pa.spec = L.work;
+  pa.twx = L.twx;
+  pa.twy = L.twy;
+  pa.mode = PLANE_FWD_REAL;
+  pa.f_in = nullptr;
+  ITP_LAUNCH(h, ITP_KERNEL_PLANE_FWD, launch_plane<R>(g, pa, h->st));
+  PencilArgs<R> pe{};
+  pe.mode = PENCIL_KINETIC;
+  pe.m = h->m;
+  pe.spec = L.work;
+  pe.kx_tab = L.htab;
+  pe.ky_tab = L.htab + g.nxh;
+  pe.kz_tab = L.htab + g.nxh + g.ny;
+  pe.scale = (R)(1.0 / (double)g.n_points);
+  pe.twz = L.twz;
+  ITP_LAUNCH(h, pe.mode == PENCIL_PROPAGATE ? ITP_KERNEL_PENCIL : ITP_KERNEL_PENCIL_KINETIC,
+                 launch_pencil<R>(g, pe, h->st));
+  PlaneArgs<R> ph = pa;
+  ph.mode = PLANE_HPSI;
+  ph.acc = h->acc;
+  ph.V = h->V;
+  ITP_LAUNCH(h, ITP_KERNEL_PLANE_HPSI, launch_plane<R>(g, ph, h->st));
+  ITP_LAUNCH(h, ITP_KERNEL_GRAM, (launch_gram_partial<R, double, R>(L.psi, h->acc, h->m, g.n_points, h->n_chunks,
+                                                   h->partial, h->st)));
+  ITP_LAUNCH(h, ITP_KERNEL_GRAM_REDUCE, launch_gram_reduce(h->partial, h->n_chunks, h->m, h->dV, 1, h->Hs, h->st));
+  if (flags & ITP_RITZ) {
+    ITP_LAUNCH(h, ITP_KERNEL_EIGH, launch_jacobi_eigh(h->Hs, h->m, h->E_dev, h->Mx, h->Wmm, h->status, h->st));
+    ITP_LAUNCH(h, ITP_KERNEL_APPLY, (launch_apply_matrix<R, R>(h->Mx, h->m, 0, L.psi, L.psi_tmp, g.n_points,
+                                             h->st)));
+    R* t = L.psi;
+    L.psi = L.psi_tmp;
+    L.psi_tmp = t;
+  } else {
+    ITP_LAUNCH(h, ITP_KERNEL_OTHER, launch_diag(h->Hs, h->m, h->E_dev, h->st));
+  }
+  return ITP_OK;
+}
+
+// Read and clear the device status word (synchronises the stream).
+int collect_status(itp_handle h) {
+  ITP_CUDA(h, cudaMemcpyAsync(h->status_host, h->status, sizeof(int), cudaMemcpyDeviceToHost,
+                              h->st));
+  ITP_CUDA(h, cudaStreamSynchronize(h->st));
+  const int s = *h->status_host;
+  if (s) {
+    ITP_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->st));
+    if (s & 1) return fail(h, ITP_ERR_NOT_PD, "overlap matrix is not positive definite");
+    if (s & 2) return fail(h, ITP_ERR_NOCONV, "Jacobi eigensolver did not converge");
+  }
+  return ITP_OK;
+}
+
+// Make the lane of precision R hold the states (converting if needed).
+template <typename R>
+int switch_lane(itp_handle h);
+template <>
+int switch_lane<double>(itp_handle h) {
+  if (h->cur64) return ITP_OK;
+  ITP_TRY(alloc_lane<double>(h, h->f64));
+  ITP_LAUNCH(h, ITP_KERNEL_OTHER, (launch_convert<float, double>(h->f32.psi, h->f64.psi,
+                                               (long long)h->m * h->g.n_points, h->st)));
+  h->cur64 = true;
+  return ITP_OK;
+}
+template <>
+int switch_lane<float>(itp_handle h) {
+  if (!h->cur64) return ITP_OK;
+  ITP_LAUNCH(h, ITP_KERNEL_OTHER, (launch_convert<double, float>(h->f64.psi, h->f32.psi,
+                                               (long long)h->m * h->g.n_points, h->st)));
+  h->cur64 = false;
+  return ITP_OK;
+}
+
+int check_ready(itp_handle h, bool need_states) {
+  if (!h) return ITP_ERR_ARG;
+  if (!h->have_V) return fail(h, ITP_ERR_STATE, "potential not set");
+  if (need_states && !h->have_states) return fail(h, ITP_ERR_STATE, "states not set");
+  ITP_CUDA(h, cudaSetDevice(h->device));
+  return ITP_OK;
+}
+
+int do_energies(itp_handle h, double* E_host, int flags) {
+  if (h->cur64) {
+    ITP_TRY(energies_lane<double>(h, flags));
+  } else {
+    ITP_TRY(energies_lane<float>(h, flags));
+  }
+  ITP_CUDA(h, cudaMemcpyAsync(h->E_host_pinned, h->E_dev, h->m * sizeof(double),
+                              cudaMemcpyDeviceToHost, h->st));
+  ITP_TRY(collect_status(h));
+  if (E_host) memcpy(E_host, h->E_host_pinned, h->m * sizeof(double));
+  return ITP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void itp_destroy(itp_handle h);
+
+int itp_create_grid(itp_handle* out, int nx, int ny, int nz, double lx, double ly, double lz,
+                    int n_states, int n_guard, int precision, void* cuda_stream) {
+  if (!out) return ITP_ERR_ARG;
+  *out = nullptr;
+  g_create_error.clear();
+  itp_handle h = new (std::nothrow) itp_grid();
+  if (!h) return ITP_ERR_OOM;
+  auto bail = [&](int code) {
+    // the message stays readable through itp_last_error(NULL)
+    g_create_error = h->err;
+    itp_destroy(h);
+    return code;
+  };
+  GridDesc& g = h->g;
+  if (!split_axis(nx, &g.rx1, &g.rx2) || !split_axis(ny, &g.ry1, &g.ry2) ||
+      !split_axis(nz, &g.rz1, &g.rz2))
+    return bail(fail(h, ITP_ERR_ARG, "unsupported grid %dx%dx%d (edges even, 2..256, "
+                                     "a product of two of 1,2,3,4,6,8,12,16)", nx, ny, nz));
+  if (!(lx > 0 && ly > 0 && lz > 0))
+    return bail(fail(h, ITP_ERR_ARG, "box lengths must be positive"));
+  if (n_states < 1 || n_guard < 0 || n_states + n_guard > kMaxStates)
+    return bail(fail(h, ITP_ERR_ARG, "need 1 <= n_states and n_states + n_guard <= %d",
+                     kMaxStates));
+  if (precision != ITP_FP64 && precision != ITP_MIXED)
+    return bail(fail(h, ITP_ERR_ARG, "unknown precision %d", precision));
+  g.nx = nx;
+  g.ny = ny;
+  g.nz = nz;
+  g.nxh = nx / 2 + 1;
+  g.n_points = (long long)nx * ny * nz;
+  g.n_half = (long long)nz * ny * g.nxh;
+  g.pp = nx + 3;   // odd pitch >= nx + 2
+  const int cbytes = precision == ITP_FP64 ? 16 : 8;
+  {
+    const size_t budget = 72 * 1024;
+    const size_t full = (size_t)nz * g.nxh * cbytes;
+    const int chunks = (int)((full + budget - 1) / budget);
+    g.pencil_w = (g.nxh + chunks - 1) / chunks;
+    g.pencil_pitch = g.pencil_w;
+  }
+  const size_t plane_bytes = plane_smem_bytes(g, cbytes / 2);
+  size_t plane64 = plane_smem_bytes(g, 8);
+  if (plane_bytes > kSmemLimit || (precision == ITP_MIXED && plane64 > kSmemLimit))
+    return bail(fail(h, ITP_ERR_ARG, "a %dx%d plane needs %zu bytes of shared memory "
+                                     "(limit %zu)", nx, ny,
+                     precision == ITP_MIXED ? plane64 : plane_bytes, kSmemLimit));
+  h->lx = lx;
+  h->ly = ly;
+  h->lz = lz;
+  h->dV = (lx / nx) * (ly / ny) * (lz / nz);
+  h->n = n_states;
+  h->ng = n_guard;
+  h->m = n_states + n_guard;
+  h->precision = precision;
+  h->st = (cudaStream_t)cuda_stream;
+  if (cudaGetDevice(&h->device) != cudaSuccess)
+    return bail(fail(h, ITP_ERR_CUDA, "no CUDA device"));
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  h->n_chunks = 2 * sms;
+  const size_t N = (size_t)g.n_points, m = (size_t)h->m;
+  int rc;
+#define ITP_CREATE(expr)           \
+  do {                             \
+    rc = (expr);                   \
+    if (rc != ITP_OK) return bail(rc); \
+  } while (0)
+  auto cuda = [&](cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return ITP_OK;
+    return fail(h, e == cudaErrorMemoryAllocation ? ITP_ERR_OOM : ITP_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+  };
+  ITP_CREATE(cuda(cudaMalloc(&h->V, N * sizeof(double)), "V"));
+  ITP_CREATE(cuda(cudaMalloc(&h->acc, m * N * sizeof(double)), "accumulator"));
+  ITP_CREATE(cuda(cudaMalloc(&h->partial, (size_t)h->n_chunks * m * m * sizeof(double)),
+                  "partials"));
+  ITP_CREATE(cuda(cudaMalloc(&h->S, m * m * sizeof(double)), "S"));
+  ITP_CREATE(cuda(cudaMalloc(&h->Mx, m * m * sizeof(double)), "M"));
+  ITP_CREATE(cuda(cudaMalloc(&h->Hs, m * m * sizeof(double)), "H_sub"));
+  ITP_CREATE(cuda(cudaMalloc(&h->Wmm, m * m * sizeof(double)), "work"));
+  ITP_CREATE(cuda(cudaMalloc(&h->E_dev, m * sizeof(double)), "E"));
+  ITP_CREATE(cuda(cudaMalloc(&h->status, sizeof(int)), "status"));
+  ITP_CREATE(cuda(cudaMemset(h->status, 0, sizeof(int)), "status"));
+  ITP_CREATE(cuda(cudaMallocHost(&h->status_host, sizeof(int)), "status (host)"));
+  ITP_CREATE(cuda(cudaMallocHost(&h->E_host_pinned, m * sizeof(double)), "E (host)"));
+  if (precision == ITP_FP64) {
+    ITP_CREATE(alloc_lane<double>(h, h->f64));
+    h->cur64 = true;
+  } else {
+    ITP_CREATE(alloc_lane<float>(h, h->f32));
+    h->cur64 = false;
+  }
+  ITP_CREATE(cuda(cudaStreamSynchronize(h->st), "create"));
+#undef ITP_CREATE
+  *out = h;
+  return ITP_OK;
+}
+
+void itp_destroy(itp_handle h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  if (h->st) cudaStreamSynchronize(h->st);
+  else cudaDeviceSynchronize();
+  free_lane(h->f32);
+  free_lane(h->f64);
+  cudaFree(h->V);
+  cudaFree(h->acc);
+  cudaFree(h->partial);
+  cudaFree(h->S);
+  cudaFree(h->Mx);
+  cudaFree(h->Hs);
+  cudaFree(h->Wmm);
+  cudaFree(h->E_dev);
+  cudaFree(h->status);
+  cudaFreeHost(h->status_host);
+  cudaFreeHost(h->E_host_pinned);
+  for (auto& e : h->prof_events) {
+    cudaEventDestroy(e.start);
+    cudaEventDestroy(e.stop);
+  }
+  delete h;
+}
+
+int itp_set_potential(itp_handle h, const double* V_host) {
+  if (!h || !V_host) return h ? fail(h, ITP_ERR_ARG, "null potential") : ITP_ERR_ARG;
+  ITP_CUDA(h, cudaSetDevice(h->device));
+  ITP_CUDA(h, cudaMemcpyAsync(h->V, V_host, (size_t)h->g.n_points * sizeof(double),
+                              cudaMemcpyHostToDevice, h->st));
+  h->f32.tab_order = 0;
+  h->f64.tab_order = 0;
+  h->have_V = true;
+  return ITP_OK;
+}
+
+static int set_states_impl(itp_handle h, const double* src, cudaMemcpyKind kind) {
+  ITP_CUDA(h, cudaSetDevice(h->device));
+  const size_t count = (size_t)h->m * h->g.n_points;
+  if (h->precision == ITP_FP64) {
+    ITP_CUDA(h, cudaMemcpyAsync(h->f64.psi, src, count * sizeof(double), kind, h->st));
+    h->cur64 = true;
+  } else {
+    ITP_CUDA(h, cudaMemcpyAsync(h->acc, src, count * sizeof(double), kind, h->st));
+    ITP_LAUNCH(h, ITP_KERNEL_OTHER, (launch_convert<double, float>(h->acc, h->f32.psi, (long long)count, h->st)));
+    h->cur64 = false;
+  }
+  h->have_states = true;
+  h->have_phi = false;
+  return ITP_OK;
+}
+
+int itp_set_states(itp_handle h, const double* psi_host) {
+  if (!h || !psi_host) return h ? fail(h, ITP_ERR_ARG, "null states") : ITP_ERR_ARG;
+  return set_states_impl(h, psi_host, cudaMemcpyHostToDevice);
+}
+
+int itp_set_states_device(itp_handle h, const double* psi_device) {
+  if (!h || !psi_device) return h ? fail(h, ITP_ERR_ARG, "null states") : ITP_ERR_ARG;
+  return set_states_impl(h, psi_device, cudaMemcpyDeviceToDevice);
+}
+
+int itp_get_states(itp_handle h, double* psi_host) {
+  if (!h || !psi_host) return h ? fail(h, ITP_ERR_ARG, "null output") : ITP_ERR_ARG;
+  if (!h->have_states) return fail(h, ITP_ERR_STATE, "states not set");
+  ITP_CUDA(h, cudaSetDevice(h->device));
+  const size_t count = (size_t)h->m * h->g.n_points;
+  const double* src = h->f64.psi;
+  if (!h->cur64) {
+    ITP_LAUNCH(h, ITP_KERNEL_OTHER, (launch_convert<float, double>(h->f32.psi, h->acc, (long long)count, h->st)));
+    src = h->acc;
+    h->have_phi = false;
+  }
+  ITP_CUDA(h, cudaMemcpyAsync(psi_host, src, count * sizeof(double), cudaMemcpyDeviceToHost,
+                              h->st));
+  return collect_status(h);
+}
+
+int itp_get_phi(itp_handle h, double* phi_host) {
+  if (!h || !phi_host) return h ? fail(h, ITP_ERR_ARG, "null output") : ITP_ERR_ARG;
+  if (!h->have_phi) return fail(h, ITP_ERR_STATE, "no propagated states pending");
+  ITP_CUDA(h, cudaSetDevice(h->device));
+  ITP_CUDA(h, cudaMemcpyAsync(phi_host, h->acc, (size_t)h->m * h->g.n_points * sizeof(double),
+                              cudaMemcpyDeviceToHost, h->st));
+  return collect_status(h);
+}
+
+int itp_propagate(itp_handle h, int order, double tau) {
+  ITP_TRY(check_ready(h, true));
+  if (order < 2 || order > 2 * kMaxTerms || (order & 1))
+    return fail(h, ITP_ERR_ARG, "order must be even, 2..%d (got %d)", 2 * kMaxTerms, order);
+  if (!(tau > 0) || !std::isfinite(tau)) return fail(h, ITP_ERR_ARG, "tau must be > 0");
+  const int k = order / 2;
+  if (h->precision == ITP_MIXED) {
+    ITP_TRY(switch_lane<float>(h));
+    ITP_TRY(propagate_lane<float>(h, k, tau));
+  } else {
+    ITP_TRY(propagate_lane<double>(h, k, tau));
+  }
+  h->have_phi = true;
+  return ITP_OK;
+}
+
+int itp_orthonormalize(itp_handle h) {
+  ITP_TRY(check_ready(h, true));
+  if (!h->have_phi) return fail(h, ITP_ERR_STATE, "no propagated states (call itp_propagate)");
+  if (h->cur64) {
+    ITP_TRY(orthonormalize_lane<double>(h));
+  } else {
+    ITP_TRY(orthonormalize_lane<float>(h));
+  }
+  h->have_phi = false;
+  return ITP_OK;
+}
+
+int itp_energies(itp_handle h, double* E_host, int flags) {
+  ITP_TRY(check_ready(h, true));
+  h->have_phi = false;
+  return do_energies(h, E_host, flags);
+}
+
+int itp_polish(itp_handle h, int order, double tau, double tol, int max_steps, int* steps_out,
+               double* E_host) {
+  ITP_TRY(check_ready(h, true));
+  if (steps_out) *steps_out = 0;
+  if (h->precision != ITP_MIXED) return fail(h, ITP_ERR_ARG, "itp_polish needs ITP_MIXED");
+  if (order < 2 || order > 2 * kMaxTerms || (order & 1) || !(tau > 0) || !(tol > 0) ||
+      max_steps < 1)
+    return fail(h, ITP_ERR_ARG, "bad polish arguments");
+  ITP_TRY(switch_lane<double>(h));
+  std::vector<double> prev(h->m), cur(h->m);
+  int step;
+  for (step = 1; step <= max_steps; ++step) {
+    ITP_TRY(propagate_lane<double>(h, order / 2, tau));
+    ITP_TRY(orthonormalize_lane<double>(h));
+    ITP_TRY(do_energies(h, cur.data(), ITP_RITZ));
+    if (step > 1) {
+      double d = 0;
+      for (int j = 0; j < h->n; ++j) d = std::fmax(d, std::fabs(cur[j] - prev[j]));
+      if (d < tol) break;
+    }
+    prev.swap(cur);
+  }
+  if (step > max_steps) {
+    step = max_steps;
+    prev.swap(cur);   // last computed energies are in prev after the final swap
+  }
+  if (steps_out) *steps_out = step;
+  if (E_host) memcpy(E_host, cur.data(), h->m * sizeof(double));
+  return ITP_OK;
+}
+
+int itp_synchronize(itp_handle h) {
+  if (!h) return ITP_ERR_ARG;
+  ITP_CUDA(h, cudaSetDevice(h->device));
+  return collect_status(h);
+}
+
+const char* itp_last_error(itp_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+long long itp_kernel_launches(itp_handle h) { return h ? h->launches : 0; }
+
+int itp_profile(itp_handle h, int enable) {
+  if (!h) return ITP_ERR_ARG;
+  ITP_CUDA(h, cudaSetDevice(h->device));
+  ITP_CUDA(h, cudaStreamSynchronize(h->st));
+  h->prof = enable != 0;
+  h->prof_used = 0;
+  return ITP_OK;
+}
+
+int itp_profile_read(itp_handle h, int kind, long long* launches, double* total_ms) {
+  if (!h || kind < 0 || kind >= ITP_KERNEL_KINDS) return h ? fail(h, ITP_ERR_ARG, "bad kind")
+                                                           : ITP_ERR_ARG;
+  ITP_CUDA(h, cudaSetDevice(h->device));
+  ITP_CUDA(h, cudaStreamSynchronize(h->st));
+  long long n = 0;
+  double ms = 0.0;
+  for (size_t i = 0; i < h->prof_used; ++i) {
+    const itp_grid::ProfEvent& e = h->prof_events[i];
+    if (e.kind != kind) continue;
+    float t = 0.f;
+    ITP_CUDA(h, cudaEventElapsedTime(&t, e.start, e.stop));
+    ms += t;
+    ++n;
+  }
+  if (launches) *launches = n;
+  if (total_ms) *total_ms = ms;
+  return ITP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+// Internal launch interface between the C-ABI layer (itp_api.cu) and the
+// device kernels (fft_passes.cu, dense.cu).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace itp {
+
+// Grid geometry and FFT plans shared by all passes of one handle.
+struct GridDesc {
+  int nx, ny, nz, nxh;       // nxh = nx/2 + 1
+  int rx1, rx2, ry1, ry2, rz1, rz2;
+  long long n_points;        // nx*ny*nz
+  long long n_half;          // nz*ny*nxh (complex)
+  int pp;                    // shared-memory pitch of a row pair (complex, odd)
+  int pencil_w;              // kx columns per pencil CTA
+  int pencil_pitch;          // shared-memory pitch of a pencil z-row (complex)
+};
+
+// Pass kinds.
+enum PlaneMode {
+  PLANE_FWD_REAL = 0,   // real state * f_in -> half spectrum
+  PLANE_MERGED = 1,     // half spectrum -> inverse -> * f_mid -> forward -> half spectrum
+  PLANE_COMBINE = 2,    // half spectrum -> inverse -> * f_out -> acc (=|+=) c * u   (FP64 acc)
+  PLANE_HPSI = 3,       // half spectrum -> inverse -> acc = u + V * psi            (FP64 acc)
+};
+
+enum PencilMode {
+  PENCIL_PROPAGATE = 0,  // * exp(-tau_i |k|^2 / 2) / N
+  PENCIL_KINETIC = 1,    // * (|k|^2 / 2) / N
+};
+
+// Arguments of one plane pass over `m` states.  R is float or double.
+template <typename R>
+struct PlaneArgs {
+  int mode;
+  int m;                     // states
+  const R* in_real;          // [m][N] real states (PLANE_FWD_REAL), also psi for PLANE_HPSI
+  void* spec;                // [m][nz][ny][nxh] complex R (in and/or out)
+  const R* f_in;             // [N] factor applied to the loaded real state (nullable)
+  const R* f_mid;            // [N] factor between inverse and forward (PLANE_MERGED)
+  const R* f_out;            // [N] factor applied before combining (PLANE_COMBINE)
+  double* acc;               // [m][N] FP64 accumulator / H psi output
+  double coef;               // c_i of the term
+  int acc_init;              // 1: acc = c*u, 0: acc += c*u
+  const double* V;           // [N] potential (PLANE_HPSI)
+  const void* twx;           // nx roots (complex R)
+  const void* twy;           // ny roots
+};
+
+template <typename R>
+struct PencilArgs {
+  int mode;
+  int m;
+  void* spec;                // [m][nz][ny][nxh] complex R, in place
+  const R* kx_tab;           // [nxh]  exp(-tau kx^2/2) or kx^2/2
+  const R* ky_tab;           // [ny]
+  const R* kz_tab;           // [nz]   (includes 1/N for PENCIL_PROPAGATE)
+  R scale;                   // 1/N for PENCIL_KINETIC
+  const void* twz;           // nz roots
+};
+
+size_t plane_smem_bytes(const GridDesc& g, int real_bytes);
+size_t pencil_smem_bytes(const GridDesc& g, int real_bytes);
+
+template <typename R>
+cudaError_t launch_plane(const GridDesc& g, const PlaneArgs<R>& a, cudaStream_t st);
+template <typename R>
+cudaError_t launch_pencil(const GridDesc& g, const PencilArgs<R>& a, cudaStream_t st);
+
+// Factor tables of one term, tau_i = tau / i:
+//   f_half = exp(-tau_i V / 2), f_full = exp(-tau_i V)   ([N] each, precision R)
+//   kx/ky/kz propagation tables (kz includes 1/N).
+template <typename R>
+cudaError_t launch_term_tables(const GridDesc& g, const double* V, double tau_i, double lx,
+                               double ly, double lz, R* f_half, R* f_full, R* kx, R* ky, R* kz,
+                               cudaStream_t st);
+// Kinetic tables kx^2/2, ky^2/2, kz^2/2.
+template <typename R>
+cudaError_t launch_kinetic_tables(const GridDesc& g, double lx, double ly, double lz, R* kx,
+                                  R* ky, R* kz, cudaStream_t st);
+
+// ---- dense part (dense.cu) ----
+// Partial Gram sums: P[c][i][j] = sum_{p in chunk c} A[i][p] * B[j][p],
+// multiplied in precision TC (FP32 products are summed in FP32 over runs of
+// 256 points and those runs in FP64).
+template <typename TA, typename TB, typename TC>
+cudaError_t launch_gram_partial(const TA* A, const TB* B, int m, long long n_points,
+                                int n_chunks, double* partial, cudaStream_t st);
+// G = scale * sum_c P[c] (fixed order), symmetrised if sym.
+cudaError_t launch_gram_reduce(const double* partial, int n_chunks, int m, double scale,
+                               int sym, double* G, cudaStream_t st);
+// Cholesky S = L L^T of an SPD m x m matrix and M = L^{-1} (lower).
+// status[0] set to 1 if a pivot is not positive (S not positive definite).
+cudaError_t launch_cholesky_inverse(const double* S, int m, double* Minv, int* status,
+                                    cudaStream_t st);
+// Symmetric eigen-decomposition (parallel cyclic Jacobi): E ascending,
+// Rt = U^T so that Rt * Psi rotates the states onto the eigenvectors.
+// work: m*m doubles.  status[0] |= 2 if the sweeps did not converge.
+cudaError_t launch_jacobi_eigh(const double* H, int m, double* E, double* Rt, double* work,
+                               int* status, cudaStream_t st);
+// E[j] = H[j][j]
+cudaError_t launch_diag(const double* H, int m, double* E, cudaStream_t st);
+// Y = M * X over all points: Y[i][p] = sum_k M[i][k] X[k][p]   (M lower
+// triangular if lower != 0), computed in the precision of TY.  X and Y must
+// not overlap.
+template <typename TX, typename TY>
+cudaError_t launch_apply_matrix(const double* M, int m, int lower, const TX* X, TY* Y,
+                                long long n_points, cudaStream_t st);
+// Precision conversion of whole state blocks.
+template <typename TS, typename TD>
+cudaError_t launch_convert(const TS* src, TD* dst, long long count, cudaStream_t st);
+
+}  // namespace itp

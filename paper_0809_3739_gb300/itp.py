@@ -1,0 +1,259 @@
+"""ctypes binding of libitp (include/itp.h): the same entry points, argument
+marshalling only.  Every step of the method runs in the CUDA library; there
+is no Python or CPU fallback, and loading fails loudly if libitp.so is
+missing."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+ITP_OK = 0
+ITP_ERR_ARG = 1
+ITP_ERR_CUDA = 2
+ITP_ERR_NOT_PD = 3
+ITP_ERR_TIMEOUT = 4
+ITP_ERR_OOM = 5
+ITP_ERR_STATE = 6
+ITP_ERR_NOCONV = 7
+ITP_FP64 = 0
+ITP_MIXED = 1
+ITP_RITZ = 1
+
+_ERR_NAMES = {1: "ITP_ERR_ARG", 2: "ITP_ERR_CUDA", 3: "ITP_ERR_NOT_PD", 4: "ITP_ERR_TIMEOUT",
+              5: "ITP_ERR_OOM", 6: "ITP_ERR_STATE", 7: "ITP_ERR_NOCONV"}
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libitp.so")
+
+# (name, restype, argtypes) of every exported entry point
+_H = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+_PD = ctypes.c_void_p
+SIGNATURES = [
+    ("itp_create_grid", _I, [ctypes.POINTER(_H), _I, _I, _I, _D, _D, _D, _I, _I, _I, ctypes.c_void_p]),
+    ("itp_destroy", None, [_H]),
+    ("itp_set_potential", _I, [_H, _PD]),
+    ("itp_set_states", _I, [_H, _PD]),
+    ("itp_set_states_device", _I, [_H, ctypes.c_void_p]),
+    ("itp_get_states", _I, [_H, _PD]),
+    ("itp_get_phi", _I, [_H, _PD]),
+    ("itp_propagate", _I, [_H, _I, _D]),
+    ("itp_orthonormalize", _I, [_H]),
+    ("itp_energies", _I, [_H, _PD, _I]),
+    ("itp_polish", _I, [_H, _I, _D, _D, _I, ctypes.POINTER(_I), _PD]),
+    ("itp_synchronize", _I, [_H]),
+    ("itp_last_error", ctypes.c_char_p, [_H]),
+    ("itp_kernel_launches", ctypes.c_longlong, [_H]),
+    ("itp_profile", _I, [_H, _I]),
+    ("itp_profile_read", _I, [_H, _I, ctypes.POINTER(ctypes.c_longlong),
+                              ctypes.POINTER(ctypes.c_double)]),
+]
+
+KERNEL_KINDS = ["plane_fwd", "plane_merged", "plane_combine", "plane_hpsi", "pencil",
+                "pencil_kinetic", "gram", "gram_reduce", "cholesky", "eigh", "apply", "other"]
+
+_lib = None
+
+
+class ItpError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"{_ERR_NAMES.get(code, code)}: {message}")
+        self.code = code
+
+
+def load() -> ctypes.CDLL:
+    """Load libitp.so (built by paper_0809_3739_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(h, code: int):
+    if code != ITP_OK:
+        msg = load().itp_last_error(h)
+        raise ItpError(code, msg.decode() if msg else "")
+
+
+def _f64(a, count=None) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if count is not None and a.size != count:
+        raise ValueError(f"expected {count} values, got {a.size}")
+    return a
+
+
+# ---- the C entry points ------------------------------------------------------
+def itp_create_grid(nx, ny, nz, lx, ly, lz, n_states, n_guard=0, precision=ITP_FP64,
+                    cuda_stream=0):
+    h = _H()
+    code = load().itp_create_grid(ctypes.byref(h), nx, ny, nz, lx, ly, lz, n_states, n_guard,
+                                  precision, ctypes.c_void_p(cuda_stream or None))
+    _check(None, code)
+    return h
+
+
+def itp_destroy(h):
+    load().itp_destroy(h)
+
+
+def itp_set_potential(h, V):
+    V = _f64(V)
+    _check(h, load().itp_set_potential(h, V.ctypes.data))
+
+
+def itp_set_states(h, psi):
+    psi = _f64(psi)
+    _check(h, load().itp_set_states(h, psi.ctypes.data))
+
+
+def itp_set_states_device(h, device_ptr: int):
+    _check(h, load().itp_set_states_device(h, ctypes.c_void_p(device_ptr)))
+
+
+def itp_get_states(h, out: np.ndarray):
+    if out.dtype != np.float64 or not out.flags.c_contiguous:
+        raise ValueError("out must be a C-contiguous float64 array")
+    _check(h, load().itp_get_states(h, out.ctypes.data))
+    return out
+
+
+def itp_get_phi(h, out: np.ndarray):
+    if out.dtype != np.float64 or not out.flags.c_contiguous:
+        raise ValueError("out must be a C-contiguous float64 array")
+    _check(h, load().itp_get_phi(h, out.ctypes.data))
+    return out
+
+
+def itp_propagate(h, order: int, tau: float):
+    _check(h, load().itp_propagate(h, int(order), float(tau)))
+
+
+def itp_orthonormalize(h):
+    _check(h, load().itp_orthonormalize(h))
+
+
+def itp_energies(h, out: np.ndarray | None, flags: int = ITP_RITZ):
+    ptr = None if out is None else out.ctypes.data
+    _check(h, load().itp_energies(h, ptr, int(flags)))
+    return out
+
+
+def itp_polish(h, order, tau, tol, max_steps, out: np.ndarray | None = None):
+    steps = _I(0)
+    ptr = None if out is None else out.ctypes.data
+    _check(h, load().itp_polish(h, int(order), float(tau), float(tol), int(max_steps),
+                                ctypes.byref(steps), ptr))
+    return steps.value
+
+
+def itp_synchronize(h):
+    _check(h, load().itp_synchronize(h))
+
+
+def itp_last_error(h) -> str:
+    r = load().itp_last_error(h)
+    return r.decode() if r else ""
+
+
+def itp_kernel_launches(h) -> int:
+    return int(load().itp_kernel_launches(h))
+
+
+def itp_profile(h, enable: bool):
+    _check(h, load().itp_profile(h, 1 if enable else 0))
+
+
+def itp_profile_read(h, kind: int):
+    n = ctypes.c_longlong(0)
+    ms = ctypes.c_double(0.0)
+    _check(h, load().itp_profile_read(h, int(kind), ctypes.byref(n), ctypes.byref(ms)))
+    return int(n.value), float(ms.value)
+
+
+# ---- a thin object wrapper -----------------------------------------------------
+class ItpGrid:
+    """One problem on the GPU: owns an itp_handle."""
+
+    def __init__(self, nx, ny, nz, lx, ly, lz, n_states, n_guard=0, precision=ITP_FP64,
+                 cuda_stream=0):
+        self.shape = (nz, ny, nx)
+        self.n_points = nx * ny * nz
+        self.n_states, self.n_guard = n_states, n_guard
+        self.m = n_states + n_guard
+        self.h = itp_create_grid(nx, ny, nz, lx, ly, lz, n_states, n_guard, precision,
+                                 cuda_stream)
+
+    def close(self):
+        if self.h:
+            itp_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_potential(self, V):
+        itp_set_potential(self.h, _f64(V, self.n_points))
+
+    def set_states(self, psi):
+        itp_set_states(self.h, _f64(psi, self.m * self.n_points))
+
+    def get_states(self):
+        out = np.empty((self.m, self.n_points), dtype=np.float64)
+        return itp_get_states(self.h, out)
+
+    def get_phi(self):
+        out = np.empty((self.m, self.n_points), dtype=np.float64)
+        return itp_get_phi(self.h, out)
+
+    def propagate(self, order, tau):
+        itp_propagate(self.h, order, tau)
+
+    def orthonormalize(self):
+        itp_orthonormalize(self.h)
+
+    def energies(self, ritz=True):
+        out = np.empty(self.m, dtype=np.float64)
+        return itp_energies(self.h, out, ITP_RITZ if ritz else 0)
+
+    def step(self, order, tau, ritz=True):
+        self.propagate(order, tau)
+        self.orthonormalize()
+        return self.energies(ritz)
+
+    def polish(self, order, tau, tol, max_steps):
+        out = np.empty(self.m, dtype=np.float64)
+        steps = itp_polish(self.h, order, tau, tol, max_steps, out)
+        return steps, out
+
+    def synchronize(self):
+        itp_synchronize(self.h)
+
+    @property
+    def kernel_launches(self):
+        return itp_kernel_launches(self.h)
+
+    def profile(self, enable=True):
+        itp_profile(self.h, enable)
+
+    def profile_read(self):
+        """{kind name: (launches, total ms)} since the last profile() call."""
+        return {name: itp_profile_read(self.h, k) for k, name in enumerate(KERNEL_KINDS)}

@@ -60,3 +60,11 @@ def test_supported_dims():
         assert supported_dim(n)
     for n in (3, 5, 10, 54, 100, 512):
         assert not supported_dim(n)
+
+
+def test_native_generator_matches_numpy():
+    import itp_workloads as W
+    W.build_native()
+    a = W.normal_states(2, 4096, seed=77, problem=3, use_native=True)
+    b = W.normal_states(2, 4096, seed=77, problem=3, use_native=False)
+    assert np.array_equal(a, b)
