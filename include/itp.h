@@ -57,7 +57,8 @@ typedef enum {
   ITP_MIXED = 1  /* FP32 FFT passes, FP64 combination / Cholesky / energies */
 } itp_precision;
 
-#define ITP_RITZ 1  /* itp_energies flag: Rayleigh-Ritz rotation of the states */
+#define ITP_RITZ 1         /* itp_energies: Ritz values, states rotated onto Ritz vectors */
+#define ITP_RITZ_VALUES 2  /* itp_energies: Ritz values only, states left as they are   */
 
 typedef struct itp_grid* itp_handle;
 
@@ -114,16 +115,24 @@ int itp_get_phi(itp_handle h, double* phi_host);
 int itp_orthonormalize(itp_handle h);
 
 /* Energies of the (orthonormal) current states, FP64 (Eq. 2):
- *   E_host[j], j < m, receives (psi_j|H|psi_j) dV, or with flags & ITP_RITZ
- *   the eigenvalues (ascending) of the subspace matrix (psi_i|H|psi_j) dV,
- *   and the states are rotated onto its eigenvectors (the subspace step of
- *   Sec. III).  E_host may be NULL.  Synchronises; returns a pending
- *   ITP_ERR_NOT_PD / ITP_ERR_NOCONV. */
+ *   flags == 0: E_host[j], j < m, receives (psi_j|H|psi_j) dV.
+ *   ITP_RITZ: the eigenvalues (ascending) of the subspace matrix
+ *     (psi_i|H|psi_j) dV, and the states are rotated onto its eigenvectors
+ *     (the subspace step of Sec. III; parallel cyclic Jacobi).
+ *   ITP_RITZ_VALUES: the same eigenvalues (Householder tridiagonalisation and
+ *     bisection), states unchanged.  The span of the states, and with it the
+ *     Ritz values of every later iteration, does not depend on the basis
+ *     (Eq. 4 keeps the span), so the rotation only matters when individual
+ *     Ritz vectors are read out: iterate with ITP_RITZ_VALUES and finish with
+ *     one ITP_RITZ.
+ *   E_host may be NULL.  Synchronises; returns a pending ITP_ERR_NOT_PD /
+ *   ITP_ERR_NOCONV. */
 int itp_energies(itp_handle h, double* E_host, int flags);
 
 /* Mixed precision only: switch the states to FP64 and iterate FP64 steps
- * (propagate, orthonormalise, Ritz energies) until
- * max_{j<n_states} |E_j - E_j(previous)| < tol or max_steps steps.
+ * (propagate, orthonormalise, Ritz values) until
+ * max_{j<n_states} |E_j - E_j(previous)| < tol or max_steps steps, then
+ * rotate the states onto the Ritz vectors (one ITP_RITZ evaluation).
  * steps_out (nullable) receives the number of steps, E_host (nullable) the
  * m final energies.  Later itp_propagate calls continue in FP32. */
 int itp_polish(itp_handle h, int order, double tau, double tol, int max_steps, int* steps_out,

@@ -268,6 +268,159 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const double* __restrict__
   }
 }
 
+// ---------------------------------------------------------------------------
+// Eigenvalues only: Householder reduction of the symmetric m x m matrix to
+// tridiagonal form (one CTA, matrix in shared memory), then bisection on
+// Sturm counts with one warp per eigenvalue (32-point multisection), spread
+// over many SMs because each SM's FP64 pipe is narrow.
+__global__ void __launch_bounds__(1024) tridiag_kernel(const double* __restrict__ H, int m,
+                                                       double* __restrict__ d,
+                                                       double* __restrict__ e) {
+  extern __shared__ double sh[];
+  const int P = m + 1;
+  double* A = sh;               // m x P
+  double* v = A + m * P;        // [m]
+  double* p = v + m;            // [m]
+  __shared__ double s_alpha, s_beta, s_K;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+  for (int q = tid; q < m * m; q += nthr) {
+    const int i = q / m, j = q - i * m;
+    A[i * P + j] = 0.5 * (H[i * m + j] + H[j * m + i]);
+  }
+  __syncthreads();
+  for (int k = 0; k + 2 < m; ++k) {
+    const int n0 = k + 1, nk = m - n0;
+    // Householder vector of x = A[n0.., k]
+    if (warp == 0) {
+      double sig = 0.0;
+      for (int i = n0 + 1 + lane; i < m; i += 32) sig += A[i * P + k] * A[i * P + k];
+      for (int o = 16; o; o >>= 1) sig += __shfl_xor_sync(0xffffffffu, sig, o);
+      if (lane == 0) {
+        const double x0 = A[n0 * P + k];
+        if (sig == 0.0) {
+          s_alpha = x0;
+          s_beta = 0.0;
+        } else {
+          const double nrm = sqrt(x0 * x0 + sig);
+          const double alpha = x0 > 0 ? -nrm : nrm;
+          const double v0 = x0 - alpha;
+          s_alpha = alpha;
+          s_beta = 2.0 / (v0 * v0 + sig);
+          v[n0] = v0;
+        }
+      }
+    }
+    __syncthreads();
+    const double beta = s_beta;
+    if (tid == 0) {
+      d[k] = A[k * P + k];
+      e[k] = s_alpha;
+    }
+    if (beta == 0.0) {   // already tridiagonal in this column
+      __syncthreads();
+      continue;
+    }
+    for (int i = n0 + 1 + tid; i < m; i += nthr) v[i] = A[i * P + k];
+    __syncthreads();
+    // p = beta * A_sub v   (one warp per row)
+    for (int i = n0 + warp; i < m; i += nw) {
+      double acc = 0.0;
+      for (int j = n0 + lane; j < m; j += 32) acc += A[i * P + j] * v[j];
+      for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) p[i] = beta * acc;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double acc = 0.0;
+      for (int i = n0 + lane; i < m; i += 32) acc += v[i] * p[i];
+      for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) s_K = 0.5 * beta * acc;
+    }
+    __syncthreads();
+    const double K = s_K;
+    for (int i = n0 + tid; i < m; i += nthr) p[i] -= K * v[i];   // p becomes w
+    __syncthreads();
+    for (int q = tid; q < nk * nk; q += nthr) {
+      const int i = n0 + q / nk, j = n0 + q % nk;
+      A[i * P + j] -= v[i] * p[j] + p[i] * v[j];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (m >= 2) {
+      d[m - 2] = A[(m - 2) * P + (m - 2)];
+      e[m - 2] = A[(m - 1) * P + (m - 2)];
+    }
+    d[m - 1] = A[(m - 1) * P + (m - 1)];
+  }
+}
+
+// Number of eigenvalues of the tridiagonal (d, e) below x (Sturm count of
+// the LDL^T pivots, with the usual guard against a zero pivot).
+__device__ __forceinline__ int sturm_count(const double* d, const double* e2, int m, double x,
+                                           double pivmin) {
+  int cnt = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  cnt += q < 0.0;
+  for (int i = 1; i < m; ++i) {
+    q = d[i] - x - e2[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    cnt += q < 0.0;
+  }
+  return cnt;
+}
+
+// One warp per eigenvalue index j: 32-point multisection of a bracket of
+// the j-th smallest eigenvalue down to a few ulps.
+__global__ void __launch_bounds__(128) bisect_kernel(const double* __restrict__ dg,
+                                                     const double* __restrict__ eg, int m,
+                                                     double* __restrict__ E) {
+  __shared__ double sd[kMaxM], se2[kMaxM];
+  __shared__ double s_lo, s_hi, s_pivmin;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < m; i += blockDim.x) {
+    sd[i] = dg[i];
+    se2[i] = i + 1 < m ? eg[i] * eg[i] : 0.0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double lo = sd[0], hi = sd[0], emax = 0.0;
+    for (int i = 0; i < m; ++i) {
+      const double r = (i > 0 ? sqrt(se2[i - 1]) : 0.0) + (i + 1 < m ? sqrt(se2[i]) : 0.0);
+      lo = fmin(lo, sd[i] - r);
+      hi = fmax(hi, sd[i] + r);
+      if (i + 1 < m) emax = fmax(emax, se2[i]);
+    }
+    const double span = fmax(hi - lo, 1e-300);
+    s_lo = lo - 1e-14 * span - 1e-300;
+    s_hi = hi + 1e-14 * span + 1e-300;
+    s_pivmin = fmax(1e-300, 2.2250738585072014e-308 * fmax(1.0, emax));
+  }
+  __syncthreads();
+  const int lane = tid & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (tid >> 5);
+  if (j >= m) return;
+  double lo = s_lo, hi = s_hi;
+  const double pivmin = s_pivmin;
+  for (int it = 0; it < 24; ++it) {
+    const double width = hi - lo;
+    if (width <= 4.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi)) + pivmin) break;
+    // 31 interior points split [lo, hi] into 32 parts
+    const double x = lo + width * (double)(lane + 1) / 32.0;
+    const int c = lane < 31 ? sturm_count(sd, se2, m, x, pivmin) : m + 1;
+    // the eigenvalue j lies in the first part whose right end has count > j
+    const unsigned ball = __ballot_sync(0xffffffffu, c > j);
+    const int first = __ffs(ball) - 1;   // 0..31 (lane 31 always votes)
+    const double nlo = first == 0 ? lo : lo + width * (double)first / 32.0;
+    const double nhi = first == 31 ? hi : lo + width * (double)(first + 1) / 32.0;
+    lo = nlo;
+    hi = nhi;
+  }
+  if (lane == 0) E[j] = 0.5 * (lo + hi);
+}
+
 __global__ void diag_kernel(const double* __restrict__ H, int m, double* __restrict__ E) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < m) E[i] = H[i * m + i];
@@ -372,6 +525,22 @@ cudaError_t launch_jacobi_eigh(const double* H, int m, double* E, double* Rt, do
                                        (int)smem);
   if (e != cudaSuccess) return e;
   jacobi_kernel<<<1, 1024, smem, st>>>(H, m, E, Rt, work, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tridiag(const double* H, int m, double* work, cudaStream_t st) {
+  if (m > kMaxM) return cudaErrorInvalidValue;
+  const size_t smem = ((size_t)m * (m + 1) + 2 * (size_t)m) * sizeof(double);
+  cudaError_t err = cudaFuncSetAttribute(tridiag_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  tridiag_kernel<<<1, 1024, smem, st>>>(H, m, work, work + m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bisect(const double* work, int m, double* E, cudaStream_t st) {
+  if (m > kMaxM) return cudaErrorInvalidValue;
+  bisect_kernel<<<(m + 3) / 4, 128, 0, st>>>(work, work + m, m, E);
   return cudaGetLastError();
 }
 

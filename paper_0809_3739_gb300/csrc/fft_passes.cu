@@ -1,23 +1,33 @@
 // Plane and pencil passes of the 3D real FFT with the split-operator factors
-// fused in (T_2 of Eq. (so) applied as point-wise multiplies around one
-// complete FFT; Sec. I).
+// fused in (T_2 of Eq. (so) as point-wise multiplies around one complete
+// FFT; Sec. I).
 //
-// Data layout in HBM:
-//   real states      [m][nz][ny][nx]        (x fastest)
-//   half spectrum    [m][nz][ny][nx/2+1]    complex, natural frequency order
-//   FP64 accumulator [m][nz][ny][nx]
+// Data layout in HBM (internal to the library):
+//   real arrays     [m][nz][nx][ny]      per-plane transposed: y fastest, so a
+//                                         "row pair" (rows y = 2r, 2r+1 at one
+//                                         x) is one contiguous (re, im) pair
+//   half spectrum   [m][nz][ny][nx/2+1]  complex, natural frequency order
+//   FP64 accumulator and potential: same layout as the real arrays.
 //
-// Plane pass: one CTA per (state, z plane).  The plane is staged in shared
-// memory as ny/2 row pairs; row pair r holds the two real rows 2r, 2r+1 as
-// one complex row (re = row 2r, im = row 2r+1) of length nx, so the real
+// Plane pass: one CTA per (state, z plane).  Rows 2r and 2r+1 travel as one
+// complex row (re = row 2r, im = row 2r+1) of length nx, so the real
 // transform along x is one complex FFT per row pair followed by the
-// even/odd split.  After the split, row pair r holds the two half-spectrum
-// rows A (row 2r) and B (row 2r+1) back to back.  The complex FFT along y
-// then runs down the nx/2+1 columns.
+// even/odd split; after the split, row pair r holds the half-spectrum rows
+// of y = 2r and y = 2r+1 back to back.  The complex FFT along y runs down
+// the nx/2+1 columns.  Global loads and stores are fused into the first and
+// last FFT stage of each pass; with the transposed real layout every such
+// access is coalesced (neighbouring lanes = neighbouring row pairs or
+// columns).
 //
-// Pencil pass: one CTA per (state, ky, block of kx columns).  The xz slab is
-// staged in shared memory; the forward FFT along z, the kinetic factor
-// exp(-tau |k|^2 / 2) / N and the inverse FFT along z all happen there.
+// Pencil pass: one CTA per (state, ky, block of kx columns).  Forward FFT
+// along z (first stage fused with the loads), then in registers the second
+// forward stage, the kinetic factor exp(-tau |k|^2/2)/N and the first
+// inverse stage, then the last inverse stage fused with the stores: two
+// shared-memory round trips per pencil.
+//
+// Kernels are specialised at compile time for the common edge lengths
+// (all index arithmetic folds to constants); a generic instantiation takes
+// the sizes at run time.
 #include "fft_common.cuh"
 #include "itp_kernels.cuh"
 
@@ -27,43 +37,243 @@ namespace {
 
 constexpr int kThreads = 256;
 
-struct RowAddr {   // x rows: transform t = row pair, element e = x
-  int pp;
-  __device__ __forceinline__ int operator()(int t, int e) const { return t * pp + e; }
+__host__ __device__ constexpr bool is_radix(int r) {
+  return r == 1 || r == 2 || r == 3 || r == 4 || r == 6 || r == 8 || r == 12 || r == 16;
+}
+// r1 of the split L = r1 * r2 (r1 <= r2, most balanced; r1 = 1 if L <= 16).
+__host__ __device__ constexpr int split_r1(int L) {
+  if (L <= 16 && is_radix(L)) return 1;
+  int best = 0;
+  for (int a = 2; a <= 16; ++a) {
+    if (!is_radix(a) || L % a) continue;
+    const int b = L / a;
+    if (!is_radix(b) || b < a) continue;
+    if (best == 0 || (b - a) < (L / best - best)) best = a;
+  }
+  return best;
+}
+
+// Compile-time (N > 0) or run-time (N == 0) axis.
+template <int N>
+struct AxisT {
+  static constexpr int L_ = N, R1_ = (N ? split_r1(N) : 0), R2_ = (N ? N / split_r1(N) : 0);
+  int L, r1, r2;
+  __device__ __forceinline__ AxisT(int l, int a, int b)
+      : L(N ? L_ : l), r1(N ? R1_ : a), r2(N ? R2_ : b) {}
 };
-struct ColAddr {   // y columns: transform t = kx, element e = y (position)
-  int pp, nxh;
-  __device__ __forceinline__ int operator()(int t, int e) const {
+
+// Threads doing FFT tasks: a multiple of the column count w (= nx/2+1 or a
+// pencil block) close to 256, so the column stages have no ragged last
+// iteration; the CTA is launched with that count rounded up to whole warps.
+__host__ __device__ constexpr int task_threads(int w) {
+  return w <= 0 ? kThreads : w * ((kThreads + w / 2) / w < 1 ? 1 : (kThreads + w / 2) / w);
+}
+__host__ __device__ constexpr int launch_threads(int nt) { return (nt + 31) / 32 * 32; }
+
+// Shared-memory pitch of a row pair: room for the padded packed row
+// (nx + nx/16) and the two half-spectrum rows (nx + 2), odd.
+__host__ __device__ constexpr int row_pitch(int nx) {
+  return ((nx + nx / 16 + 2) % 2) ? nx + nx / 16 + 2 : nx + nx / 16 + 3;
+}
+// CTAs per SM that the shared memory of a specialised pass allows (the
+// register budget follows from it through __launch_bounds__).
+__host__ __device__ constexpr int min_blocks(long long smem_bytes, int cap) {
+  return smem_bytes <= 0 ? 1
+         : (227LL * 1024 / smem_bytes) < 1 ? 1
+         : (227LL * 1024 / smem_bytes) > cap ? cap
+         : (int)(227LL * 1024 / smem_bytes);
+}
+__host__ __device__ constexpr long long plane_smem_ct(int nx, int ny, int rbytes) {
+  return nx ? ((long long)(ny / 2) * row_pitch(nx) + nx + ny) * 2 * rbytes : 0;
+}
+__host__ __device__ constexpr long long pencil_smem_ct(int nz, int w, int rbytes) {
+  return nz ? ((long long)nz * w + nz) * 2 * rbytes : 0;
+}
+
+// Padded position of element p of a packed row: one pad slot per 16 keeps
+// the strided reads of the split/merge free of bank conflicts.
+__device__ __forceinline__ int swz(int p) { return p + (p >> 4); }
+
+// Task loop over NT threads: task = t + ntr * q, t fastest across lanes.
+template <int NT, typename F>
+__device__ __forceinline__ void for_tasks(int ntr, int nq, F&& f) {
+  const int total = ntr * nq;
+  if (threadIdx.x >= NT) return;
+  for (int task = threadIdx.x; task < total; task += NT) {
+    const int q = task / ntr;
+    const int t = task - q * ntr;
+    f(t, q);
+  }
+}
+
+// Radix dispatch: FN<r>(args...) for the run-time radix r (folds to one case
+// when r is a compile-time constant).
+#define ITP_WITH_RADIX(r, FN, ...)          \
+  switch (r) {                              \
+    case 1: FN<1>(__VA_ARGS__); break;      \
+    case 2: FN<2>(__VA_ARGS__); break;      \
+    case 3: FN<3>(__VA_ARGS__); break;      \
+    case 4: FN<4>(__VA_ARGS__); break;      \
+    case 6: FN<6>(__VA_ARGS__); break;      \
+    case 8: FN<8>(__VA_ARGS__); break;      \
+    case 12: FN<12>(__VA_ARGS__); break;    \
+    case 16: FN<16>(__VA_ARGS__); break;    \
+    default: break;                         \
+  }
+
+template <typename C>
+__device__ __forceinline__ C cscale(C a, decltype(a.x) s) {
+  a.x *= s;
+  a.y *= s;
+  return a;
+}
+template <typename C>
+__device__ __forceinline__ C cmulri(C a, C f) {  // (a.x * f.x, a.y * f.y)
+  a.x *= f.x;
+  a.y *= f.y;
+  return a;
+}
+
+// ----------------------------------------------------------------------------
+// Shared-memory geometry of one plane.
+template <typename R, int NX, int NY>
+struct PlaneGeo {
+  using C = typename CplxOf<R>::type;
+  static constexpr int NT = kThreads;
+  AxisT<NX> ax;
+  AxisT<NY> ay;
+  int nx, ny, nxh, npair, pp;
+  __device__ __forceinline__ PlaneGeo(const GridDesc& g)
+      : ax(g.nx, g.rx1, g.rx2), ay(g.ny, g.ry1, g.ry2) {
+    nx = NX ? NX : g.nx;
+    ny = NY ? NY : g.ny;
+    nxh = nx / 2 + 1;
+    npair = ny / 2;
+    pp = NX ? row_pitch(NX) : g.pp;
+  }
+  // x rows: transform t = row pair, element e = x (padded)
+  __device__ __forceinline__ int row(int t, int e) const { return t * pp + swz(e); }
+  // y columns: transform t = kx, element e = y position
+  __device__ __forceinline__ int col(int t, int e) const {
     return (e >> 1) * pp + (e & 1) * nxh + t;
   }
 };
-struct SlabAddr {  // z columns of a pencil slab: transform t = kx column, element e = z
-  int pitch;
-  __device__ __forceinline__ int operator()(int t, int e) const { return e * pitch + t; }
-};
 
-template <typename R> struct Vec2Of;
-template <> struct Vec2Of<float> { using type = float2; };
-template <> struct Vec2Of<double> { using type = double2; };
+// ---- x stages (rows), all in shared memory except the fused ends ------------
+// Forward stage A with the global load fused in: element x of row pair t is
+// the pair (psi[y=2t][x], psi[y=2t+1][x]) = src[x * npair + t] (transposed
+// layout), times the factor pair f[x * npair + t].
+template <int R2, typename R, int NX, int NY, typename C>
+__device__ __forceinline__ void xA_fwd_global_r(const PlaneGeo<R, NX, NY>& G, C* sm,
+                                                const C* __restrict__ src,
+                                                const C* __restrict__ f, const C* tw) {
+  constexpr int NT = PlaneGeo<R, NX, NY>::NT;
+  for_tasks<NT>(G.npair, G.ax.r1, [&](int t, int n1) {
+    C a[R2];
+#pragma unroll
+    for (int j = 0; j < R2; ++j) {
+      const int x = n1 + G.ax.r1 * j;
+      a[j] = src[x * G.npair + t];
+      if (f) a[j] = cmulri(a[j], __ldg(&f[x * G.npair + t]));
+    }
+    Dft<R2, -1, C>::run(a);
+    if (G.ax.r1 > 1) {
+#pragma unroll
+      for (int j = 1; j < R2; ++j) a[j] = cmul(a[j], tw[n1 * j]);
+    }
+#pragma unroll
+    for (int j = 0; j < R2; ++j) sm[G.row(t, n1 + G.ax.r1 * j)] = a[j];
+  });
+}
+template <typename R, int NX, int NY, typename C>
+__device__ __forceinline__ void xA_fwd_global(const PlaneGeo<R, NX, NY>& G, C* sm,
+                                              const C* __restrict__ src,
+                                              const C* __restrict__ f, const C* tw) {
+  ITP_WITH_RADIX(G.ax.r2, xA_fwd_global_r, G, sm, src, f, tw)
+}
 
-// Real transform along x, forward: split each row pair's spectrum Z of the
-// packed row (a + i b) into A = FFT(a), B = FFT(b), k = 0..nx/2.
-// One warp per row pair; Z is read in digit-swapped order.
-template <typename C>
-__device__ __forceinline__ void x_split(C* sm, int npair, int pp, int nx, int nxh, const Axis ax) {
-  using Rl = decltype(sm[0].x);
-  constexpr int MAXQ = 5;   // (nx/2 + 1) <= 32 * MAXQ  for nx <= 256
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int half = nx >> 1;
-  for (int r = warp; r < npair; r += nw) {
-    C* row = sm + r * pp;
+// Stage B (DIR = -1 forward, +1 inverse with the conjugate twiddle after).
+template <int R1, int DIR, typename R, int NX, int NY, typename C>
+__device__ __forceinline__ void xB_r(const PlaneGeo<R, NX, NY>& G, C* sm, const C* tw) {
+  constexpr int NT = PlaneGeo<R, NX, NY>::NT;
+  for_tasks<NT>(G.npair, G.ax.r2, [&](int t, int b) {
+    C a[R1];
+#pragma unroll
+    for (int i = 0; i < R1; ++i) a[i] = sm[G.row(t, i + R1 * b)];
+    Dft<R1, DIR, C>::run(a);
+    if (DIR > 0) {
+#pragma unroll
+      for (int i = 1; i < R1; ++i) a[i] = cmulc(a[i], tw[i * b]);
+    }
+#pragma unroll
+    for (int i = 0; i < R1; ++i) sm[G.row(t, i + R1 * b)] = a[i];
+  });
+}
+template <int R1, typename G_, typename C>
+__device__ __forceinline__ void xB_fwd_r(const G_& G, C* sm, const C* tw) { xB_r<R1, -1>(G, sm, tw); }
+template <int R1, typename G_, typename C>
+__device__ __forceinline__ void xB_inv_r(const G_& G, C* sm, const C* tw) { xB_r<R1, 1>(G, sm, tw); }
+template <int DIR, typename R, int NX, int NY, typename C>
+__device__ __forceinline__ void xB(const PlaneGeo<R, NX, NY>& G, C* sm, const C* tw) {
+  if (G.ax.r1 == 1) return;
+  if (DIR < 0) {
+    ITP_WITH_RADIX(G.ax.r1, xB_fwd_r, G, sm, tw)
+  } else {
+    ITP_WITH_RADIX(G.ax.r1, xB_inv_r, G, sm, tw)
+  }
+}
+
+// Inverse stage A' followed by an epilogue on the natural-order row data:
+// epi.apply<R2>(t, n1, a) receives a[j] = element x = n1 + r1*j of row pair
+// t and either stores it somewhere (returns false) or transforms it and asks
+// for the forward stage A to follow in registers (returns true).
+template <int R2, typename R, int NX, int NY, typename C, typename Epi>
+__device__ __forceinline__ void xA_inv_then_r(const PlaneGeo<R, NX, NY>& G, C* sm, const C* tw,
+                                              const Epi& epi) {
+  constexpr int NT = PlaneGeo<R, NX, NY>::NT;
+  for_tasks<NT>(G.npair, G.ax.r1, [&](int t, int n1) {
+    C a[R2];
+#pragma unroll
+    for (int j = 0; j < R2; ++j) a[j] = sm[G.row(t, n1 + G.ax.r1 * j)];
+    Dft<R2, 1, C>::run(a);
+    if (epi.template apply<R2>(t, n1, a)) {
+      Dft<R2, -1, C>::run(a);
+      if (G.ax.r1 > 1) {
+#pragma unroll
+        for (int j = 1; j < R2; ++j) a[j] = cmul(a[j], tw[n1 * j]);
+      }
+#pragma unroll
+      for (int j = 0; j < R2; ++j) sm[G.row(t, n1 + G.ax.r1 * j)] = a[j];
+    }
+  });
+}
+template <typename R, int NX, int NY, typename C, typename Epi>
+__device__ __forceinline__ void xA_inv_then(const PlaneGeo<R, NX, NY>& G, C* sm, const C* tw,
+                                            const Epi& epi) {
+  ITP_WITH_RADIX(G.ax.r2, xA_inv_then_r, G, sm, tw, epi)
+}
+
+// Real transform along x, forward: split the spectrum Z of each packed row
+// (a + i b) into A = FFT(a), B = FFT(b), k = 0..nx/2.  One warp per row
+// pair; Z is read in digit-swapped order.
+template <typename R, int NX, int NY>
+__device__ __forceinline__ void x_split(const PlaneGeo<R, NX, NY>& G, typename CplxOf<R>::type* sm) {
+  using C = typename CplxOf<R>::type;
+  constexpr int MAXQ = NX ? (NX / 2 + 32) / 32 : 5;
+  constexpr int NW = PlaneGeo<R, NX, NY>::NT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int half = G.nx >> 1;
+  const Axis ax{G.ax.L, G.ax.r1, G.ax.r2};
+  if (warp >= NW) return;
+  for (int r = warp; r < G.npair; r += NW) {
+    C* row = sm + r * G.pp;
     C zp[MAXQ], zm[MAXQ];
 #pragma unroll
     for (int q = 0; q < MAXQ; ++q) {
       const int k = lane + 32 * q;
       if (k <= half) {
-        zp[q] = row[spec_pos(ax, k)];
-        zm[q] = row[spec_pos(ax, k == 0 ? 0 : nx - k)];
+        zp[q] = row[swz(spec_pos(ax, k))];
+        zm[q] = row[swz(spec_pos(ax, k == 0 ? 0 : G.nx - k))];
       }
     }
     __syncwarp();
@@ -71,37 +281,40 @@ __device__ __forceinline__ void x_split(C* sm, int npair, int pp, int nx, int nx
     for (int q = 0; q < MAXQ; ++q) {
       const int k = lane + 32 * q;
       if (k <= half) {
-        // A = (Z[k] + conj(Z[-k])) / 2,  B = (Z[k] - conj(Z[-k])) / (2i)
         C A, B;
-        A.x = (Rl)0.5 * (zp[q].x + zm[q].x);
-        A.y = (Rl)0.5 * (zp[q].y - zm[q].y);
-        B.x = (Rl)0.5 * (zp[q].y + zm[q].y);
-        B.y = (Rl)0.5 * (zm[q].x - zp[q].x);
+        A.x = (R)0.5 * (zp[q].x + zm[q].x);
+        A.y = (R)0.5 * (zp[q].y - zm[q].y);
+        B.x = (R)0.5 * (zp[q].y + zm[q].y);
+        B.y = (R)0.5 * (zm[q].x - zp[q].x);
         row[k] = A;
-        row[nxh + k] = B;
+        row[G.nxh + k] = B;
       }
     }
     __syncwarp();
   }
 }
 
-// Inverse of x_split: build Z = A + iB over all nx frequencies (Hermitian
-// extension; the imaginary parts of the self-conjugate bins k = 0, nx/2 are
-// dropped, as a complex-to-real transform does) in digit-swapped order.
-template <typename C>
-__device__ __forceinline__ void x_merge(C* sm, int npair, int pp, int nx, int nxh, const Axis ax) {
-  constexpr int MAXQ = 5;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int half = nx >> 1;
-  for (int r = warp; r < npair; r += nw) {
-    C* row = sm + r * pp;
+// Inverse of x_split (Hermitian extension; the imaginary parts of the
+// self-conjugate bins k = 0, nx/2 are dropped, as a complex-to-real
+// transform does), writing Z in digit-swapped order.
+template <typename R, int NX, int NY>
+__device__ __forceinline__ void x_merge(const PlaneGeo<R, NX, NY>& G, typename CplxOf<R>::type* sm) {
+  using C = typename CplxOf<R>::type;
+  constexpr int MAXQ = NX ? (NX / 2 + 32) / 32 : 5;
+  constexpr int NW = PlaneGeo<R, NX, NY>::NT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int half = G.nx >> 1;
+  const Axis ax{G.ax.L, G.ax.r1, G.ax.r2};
+  if (warp >= NW) return;
+  for (int r = warp; r < G.npair; r += NW) {
+    C* row = sm + r * G.pp;
     C av[MAXQ], bv[MAXQ];
 #pragma unroll
     for (int q = 0; q < MAXQ; ++q) {
       const int k = lane + 32 * q;
       if (k <= half) {
         av[q] = row[k];
-        bv[q] = row[nxh + k];
+        bv[q] = row[G.nxh + k];
       }
     }
     __syncwarp();
@@ -114,12 +327,12 @@ __device__ __forceinline__ void x_merge(C* sm, int npair, int pp, int nx, int nx
         C Z;
         Z.x = A.x - B.y;
         Z.y = A.y + B.x;
-        row[spec_pos(ax, k)] = Z;
+        row[swz(spec_pos(ax, k))] = Z;
         if (k > 0 && k < half) {
           C Zm;
           Zm.x = A.x + B.y;
           Zm.y = B.x - A.y;
-          row[spec_pos(ax, nx - k)] = Zm;
+          row[swz(spec_pos(ax, G.nx - k))] = Zm;
         }
       }
     }
@@ -127,173 +340,355 @@ __device__ __forceinline__ void x_merge(C* sm, int npair, int pp, int nx, int nx
   }
 }
 
-template <typename R, int MODE>
-__global__ void __launch_bounds__(kThreads) plane_kernel(const GridDesc g, const PlaneArgs<R> a) {
+// ---- y stages (columns) -------------------------------------------------------
+// Inverse stage B' with the global load fused in: column t, block b reads
+// the frequencies ky = b + r2*a (a < r1) straight from the half spectrum.
+template <int R1, typename R, int NX, int NY, typename C>
+__device__ __forceinline__ void yB_inv_global_r(const PlaneGeo<R, NX, NY>& G, C* sm,
+                                                const C* __restrict__ spec, const C* tw) {
+  constexpr int NT = PlaneGeo<R, NX, NY>::NT;
+  for_tasks<NT>(G.nxh, G.ay.r2, [&](int t, int b) {
+    C a[R1];
+#pragma unroll
+    for (int i = 0; i < R1; ++i) a[i] = spec[(b + G.ay.r2 * i) * G.nxh + t];
+    Dft<R1, 1, C>::run(a);
+    if (R1 > 1) {
+#pragma unroll
+      for (int i = 1; i < R1; ++i) a[i] = cmulc(a[i], tw[i * b]);
+    }
+#pragma unroll
+    for (int i = 0; i < R1; ++i) sm[G.col(t, i + R1 * b)] = a[i];
+  });
+}
+template <typename R, int NX, int NY, typename C>
+__device__ __forceinline__ void yB_inv_global(const PlaneGeo<R, NX, NY>& G, C* sm,
+                                              const C* __restrict__ spec, const C* tw) {
+  ITP_WITH_RADIX(G.ay.r1, yB_inv_global_r, G, sm, spec, tw)
+}
+
+// Stage A on columns (DIR = -1 forward with twiddle after; +1 inverse).
+template <int R2, int DIR, typename R, int NX, int NY, typename C>
+__device__ __forceinline__ void yA_r(const PlaneGeo<R, NX, NY>& G, C* sm, const C* tw) {
+  constexpr int NT = PlaneGeo<R, NX, NY>::NT;
+  for_tasks<NT>(G.nxh, G.ay.r1, [&](int t, int n1) {
+    C a[R2];
+#pragma unroll
+    for (int j = 0; j < R2; ++j) a[j] = sm[G.col(t, n1 + G.ay.r1 * j)];
+    Dft<R2, DIR, C>::run(a);
+    if (DIR < 0 && G.ay.r1 > 1) {
+#pragma unroll
+      for (int j = 1; j < R2; ++j) a[j] = cmul(a[j], tw[n1 * j]);
+    }
+#pragma unroll
+    for (int j = 0; j < R2; ++j) sm[G.col(t, n1 + G.ay.r1 * j)] = a[j];
+  });
+}
+template <int R2, typename G_, typename C>
+__device__ __forceinline__ void yA_fwd_r(const G_& G, C* sm, const C* tw) { yA_r<R2, -1>(G, sm, tw); }
+template <int R2, typename G_, typename C>
+__device__ __forceinline__ void yA_inv_r(const G_& G, C* sm, const C* tw) { yA_r<R2, 1>(G, sm, tw); }
+template <int DIR, typename R, int NX, int NY, typename C>
+__device__ __forceinline__ void yA(const PlaneGeo<R, NX, NY>& G, C* sm, const C* tw) {
+  if (DIR < 0) {
+    ITP_WITH_RADIX(G.ay.r2, yA_fwd_r, G, sm, tw)
+  } else {
+    ITP_WITH_RADIX(G.ay.r2, yA_inv_r, G, sm, tw)
+  }
+}
+
+// Forward stage B with the global store fused in: column t, block b writes
+// the frequencies ky = b + r2*k1 to the half spectrum.
+template <int R1, typename R, int NX, int NY, typename C>
+__device__ __forceinline__ void yB_fwd_global_r(const PlaneGeo<R, NX, NY>& G, C* sm,
+                                                C* __restrict__ spec) {
+  constexpr int NT = PlaneGeo<R, NX, NY>::NT;
+  for_tasks<NT>(G.nxh, G.ay.r2, [&](int t, int b) {
+    C a[R1];
+#pragma unroll
+    for (int i = 0; i < R1; ++i) a[i] = sm[G.col(t, i + R1 * b)];
+    Dft<R1, -1, C>::run(a);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) spec[(b + G.ay.r2 * k1) * G.nxh + t] = a[k1];
+  });
+}
+template <typename R, int NX, int NY, typename C>
+__device__ __forceinline__ void yB_fwd_global(const PlaneGeo<R, NX, NY>& G, C* sm,
+                                              C* __restrict__ spec) {
+  ITP_WITH_RADIX(G.ay.r1, yB_fwd_global_r, G, sm, spec)
+}
+
+// ---- epilogues of the inverse x transform -------------------------------------
+// PLANE_MERGED: multiply by exp(-tau_i V) (pairs in the transposed layout)
+// and continue with the forward stage A.
+template <typename R>
+struct EpiMerged {
   using C = typename CplxOf<R>::type;
-  using V2 = typename Vec2Of<R>::type;
+  const C* f;
+  int npair, r1;
+  template <int R2> __device__ __forceinline__ bool apply(int t, int n1, C* a) const {
+#pragma unroll
+    for (int j = 0; j < R2; ++j) a[j] = cmulri(a[j], __ldg(&f[(n1 + r1 * j) * npair + t]));
+    return true;
+  }
+};
+// PLANE_COMBINE: acc (=|+=) c * f_out * u in FP64; with phi set, the
+// finished sum goes to phi in precision R instead of back to acc.
+template <typename R>
+struct EpiCombine {
+  using C = typename CplxOf<R>::type;
+  const C* f;
+  double2* acc;
+  C* phi;
+  double c;
+  int init, npair, r1;
+  template <int R2> __device__ __forceinline__ bool apply(int t, int n1, C* a) const {
+#pragma unroll
+    for (int j = 0; j < R2; ++j) {
+      const int idx = (n1 + r1 * j) * npair + t;
+      const C u = cmulri(a[j], __ldg(&f[idx]));
+      double2 v;
+      v.x = c * (double)u.x;
+      v.y = c * (double)u.y;
+      if (!init) {
+        const double2 o = acc[idx];
+        v.x += o.x;
+        v.y += o.y;
+      }
+      if (phi) {
+        C w;
+        w.x = (R)v.x;
+        w.y = (R)v.y;
+        phi[idx] = w;
+      } else {
+        acc[idx] = v;
+      }
+    }
+    return false;
+  }
+};
+// PLANE_TERM: the term's scaled contribution c * f_out * u, rounded to
+// precision R, written over the term's own spectrum plane (its real plane
+// fits in the half-spectrum plane; all of the plane was read before).
+template <typename R>
+struct EpiTerm {
+  using C = typename CplxOf<R>::type;
+  const C* f;
+  C* out;
+  double c;
+  int npair, r1;
+  template <int R2> __device__ __forceinline__ bool apply(int t, int n1, C* a) const {
+#pragma unroll
+    for (int j = 0; j < R2; ++j) {
+      const int idx = (n1 + r1 * j) * npair + t;
+      const C u = cmulri(a[j], __ldg(&f[idx]));
+      C w;
+      w.x = (R)(c * (double)u.x);
+      w.y = (R)(c * (double)u.y);
+      out[idx] = w;
+    }
+    return false;
+  }
+};
+
+// PLANE_HPSI: out = u + V * psi in FP64.
+template <typename R>
+struct EpiHpsi {
+  using C = typename CplxOf<R>::type;
+  const C* psi;
+  const double2* V;
+  double2* out;
+  int npair, r1;
+  template <int R2> __device__ __forceinline__ bool apply(int t, int n1, C* a) const {
+#pragma unroll
+    for (int j = 0; j < R2; ++j) {
+      const int idx = (n1 + r1 * j) * npair + t;
+      const C q = psi[idx];
+      const double2 v = __ldg(&V[idx]);
+      double2 h;
+      h.x = (double)a[j].x + v.x * (double)q.x;
+      h.y = (double)a[j].y + v.y * (double)q.y;
+      out[idx] = h;
+    }
+    return false;
+  }
+};
+
+template <typename R, int NX, int NY, int MODE>
+__global__ void __launch_bounds__(launch_threads(PlaneGeo<R, NX, NY>::NT),
+                                  min_blocks(plane_smem_ct(NX, NY, sizeof(R)),
+                                             sizeof(R) == 4 ? 3 : 2))
+    plane_kernel(const GridDesc g, const PlaneArgs<R> a) {
+  using C = typename CplxOf<R>::type;
   extern __shared__ __align__(16) unsigned char smraw[];
+  const PlaneGeo<R, NX, NY> G(g);
   C* sm = reinterpret_cast<C*>(smraw);
+  C* twx = sm + G.npair * G.pp;   // nx roots
+  C* twy = twx + G.nx;            // ny roots
+  for (int i = threadIdx.x; i < G.nx; i += blockDim.x) twx[i] = static_cast<const C*>(a.twx)[i];
+  for (int i = threadIdx.x; i < G.ny; i += blockDim.x) twy[i] = static_cast<const C*>(a.twy)[i];
 
   const int z = blockIdx.x, s = blockIdx.y;
-  const int nx = g.nx, ny = g.ny, nxh = g.nxh, pp = g.pp;
-  const int npair = ny >> 1, hx = nx >> 1;
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const long long N = g.n_points;
-  const long long plane_off = (long long)z * ny * nx;
-  const long long spec_off = ((long long)s * g.nz + z) * (long long)ny * nxh;
-  const Axis axx{nx, g.rx1, g.rx2}, axy{ny, g.ry1, g.ry2};
-  const C* twx = static_cast<const C*>(a.twx);
-  const C* twy = static_cast<const C*>(a.twy);
-  const RowAddr rows{pp};
-  const ColAddr cols{pp, nxh};
+  const long long plane_pts = (long long)G.nx * G.ny;
+  const long long real_off = (long long)s * g.n_points + (long long)z * plane_pts;
+  const long long spec_off = ((long long)s * g.nz + z) * (long long)G.ny * G.nxh;
+  const long long fac_off = (long long)z * plane_pts;
+  __syncthreads();
 
   if constexpr (MODE == PLANE_FWD_REAL) {
-    const R* src = a.in_real + (long long)s * N + plane_off;
-    const R* f = a.f_in ? a.f_in + plane_off : nullptr;
-    for (int idx = tid; idx < npair * hx; idx += nthr) {
-      const int r = idx / hx, x = 2 * (idx - r * hx);
-      V2 va = *reinterpret_cast<const V2*>(src + (2 * r) * nx + x);
-      V2 vb = *reinterpret_cast<const V2*>(src + (2 * r + 1) * nx + x);
-      if (f) {
-        const V2 fa = __ldg(reinterpret_cast<const V2*>(f + (2 * r) * nx + x));
-        const V2 fb = __ldg(reinterpret_cast<const V2*>(f + (2 * r + 1) * nx + x));
-        va.x *= fa.x; va.y *= fa.y; vb.x *= fb.x; vb.y *= fb.y;
-      }
-      C c0, c1;
-      c0.x = va.x; c0.y = vb.x;
-      c1.x = va.y; c1.y = vb.y;
-      sm[r * pp + x] = c0;
-      sm[r * pp + x + 1] = c1;
-    }
+    const C* src = reinterpret_cast<const C*>(a.in_real + real_off);
+    const C* f = a.f_in ? reinterpret_cast<const C*>(a.f_in + fac_off) : nullptr;
+    xA_fwd_global(G, sm, src, f, twx);
     __syncthreads();
   } else {
-    const C* src = static_cast<const C*>(a.spec) + spec_off;
-    for (int idx = tid; idx < ny * nxh; idx += nthr) {
-      const int ky = idx / nxh, kx = idx - ky * nxh;
-      sm[cols(kx, spec_pos(axy, ky))] = src[idx];
-    }
+    const C* spec = static_cast<const C*>(a.spec) + spec_off;
+    yB_inv_global(G, sm, spec, twy);
     __syncthreads();
-    fft_inverse(sm, cols, nxh, axy, twy);
-    x_merge(sm, npair, pp, nx, nxh, axx);
+    yA<1>(G, sm, twy);
     __syncthreads();
-    fft_inverse(sm, rows, npair, axx, twx);
-
-    if constexpr (MODE == PLANE_COMBINE) {
-      double* acc = a.acc + (long long)s * N + plane_off;
-      const R* f = a.f_out + plane_off;
-      const double c = a.coef;
-      for (int idx = tid; idx < npair * hx; idx += nthr) {
-        const int r = idx / hx, x = 2 * (idx - r * hx);
-        const C v0 = sm[r * pp + x], v1 = sm[r * pp + x + 1];
-        const V2 fa = __ldg(reinterpret_cast<const V2*>(f + (2 * r) * nx + x));
-        const V2 fb = __ldg(reinterpret_cast<const V2*>(f + (2 * r + 1) * nx + x));
-        double2* pa = reinterpret_cast<double2*>(acc + (2 * r) * nx + x);
-        double2* pb = reinterpret_cast<double2*>(acc + (2 * r + 1) * nx + x);
-        double2 ua, ub;
-        ua.x = c * (double)(v0.x * fa.x); ua.y = c * (double)(v1.x * fa.y);
-        ub.x = c * (double)(v0.y * fb.x); ub.y = c * (double)(v1.y * fb.y);
-        if (!a.acc_init) {
-          const double2 oa = *pa, ob = *pb;
-          ua.x += oa.x; ua.y += oa.y; ub.x += ob.x; ub.y += ob.y;
-        }
-        *pa = ua;
-        *pb = ub;
-      }
+    x_merge(G, sm);
+    __syncthreads();
+    xB<1>(G, sm, twx);
+    __syncthreads();
+    if constexpr (MODE == PLANE_MERGED) {
+      EpiMerged<R> epi{reinterpret_cast<const C*>(a.f_mid + fac_off), G.npair, G.ax.r1};
+      xA_inv_then(G, sm, twx, epi);
+      __syncthreads();
+    } else if constexpr (MODE == PLANE_TERM) {
+      EpiTerm<R> epi{reinterpret_cast<const C*>(a.f_out + fac_off),
+                     static_cast<C*>(a.spec) + spec_off, a.coef, G.npair, G.ax.r1};
+      xA_inv_then(G, sm, twx, epi);
       return;
-    } else if constexpr (MODE == PLANE_HPSI) {
-      double* out = a.acc + (long long)s * N + plane_off;
-      const R* psi = a.in_real + (long long)s * N + plane_off;
-      const double* V = a.V + plane_off;
-      for (int idx = tid; idx < npair * hx; idx += nthr) {
-        const int r = idx / hx, x = 2 * (idx - r * hx);
-        const C v0 = sm[r * pp + x], v1 = sm[r * pp + x + 1];
-        const V2 qa = *reinterpret_cast<const V2*>(psi + (2 * r) * nx + x);
-        const V2 qb = *reinterpret_cast<const V2*>(psi + (2 * r + 1) * nx + x);
-        const double2 Va = __ldg(reinterpret_cast<const double2*>(V + (2 * r) * nx + x));
-        const double2 Vb = __ldg(reinterpret_cast<const double2*>(V + (2 * r + 1) * nx + x));
-        double2 ha, hb;
-        ha.x = (double)v0.x + Va.x * (double)qa.x;
-        ha.y = (double)v1.x + Va.y * (double)qa.y;
-        hb.x = (double)v0.y + Vb.x * (double)qb.x;
-        hb.y = (double)v1.y + Vb.y * (double)qb.y;
-        *reinterpret_cast<double2*>(out + (2 * r) * nx + x) = ha;
-        *reinterpret_cast<double2*>(out + (2 * r + 1) * nx + x) = hb;
-      }
+    } else if constexpr (MODE == PLANE_COMBINE) {
+      EpiCombine<R> epi{reinterpret_cast<const C*>(a.f_out + fac_off),
+                        reinterpret_cast<double2*>(a.acc + real_off),
+                        a.phi_out ? reinterpret_cast<C*>(a.phi_out + real_off) : nullptr,
+                        a.coef, a.acc_init, G.npair, G.ax.r1};
+      xA_inv_then(G, sm, twx, epi);
       return;
     } else {
-      // PLANE_MERGED: the two adjacent half steps exp(-tau_i V/2) merge into
-      // one exp(-tau_i V) between the inverse and the next forward FFT.
-      const R* f = a.f_mid + plane_off;
-      for (int idx = tid; idx < npair * nx; idx += nthr) {
-        const int r = idx / nx, x = idx - r * nx;
-        C v = sm[r * pp + x];
-        v.x *= __ldg(f + (2 * r) * nx + x);
-        v.y *= __ldg(f + (2 * r + 1) * nx + x);
-        sm[r * pp + x] = v;
-      }
-      __syncthreads();
+      EpiHpsi<R> epi{reinterpret_cast<const C*>(a.in_real + real_off),
+                     reinterpret_cast<const double2*>(a.V + fac_off),
+                     reinterpret_cast<double2*>(a.acc + real_off), G.npair, G.ax.r1};
+      xA_inv_then(G, sm, twx, epi);
+      return;
     }
   }
-
-  if constexpr (MODE == PLANE_FWD_REAL || MODE == PLANE_MERGED) {
-    fft_forward(sm, rows, npair, axx, twx);
-    x_split(sm, npair, pp, nx, nxh, axx);
-    __syncthreads();
-    fft_forward(sm, cols, nxh, axy, twy);
-    C* dst = static_cast<C*>(a.spec) + spec_off;
-    for (int idx = tid; idx < ny * nxh; idx += nthr) {
-      const int ky = idx / nxh, kx = idx - ky * nxh;
-      dst[idx] = sm[cols(kx, spec_pos(axy, ky))];
-    }
-  }
+  // forward x (stage B), split, forward y
+  xB<-1>(G, sm, twx);
+  __syncthreads();
+  x_split(G, sm);
+  __syncthreads();
+  yA<-1>(G, sm, twy);
+  __syncthreads();
+  yB_fwd_global(G, sm, static_cast<C*>(a.spec) + spec_off);
 }
 
-template <typename R, int MODE>
-__global__ void __launch_bounds__(kThreads) pencil_kernel(const GridDesc g, const PencilArgs<R> a) {
+// ----------------------------------------------------------------------------
+// Pencil stages.  Slab element (z, column t) at shared position z * pw + t.
+template <int M> struct mode_tag {};
+
+// forward stage A, loads fused
+template <int NT> struct nt_tag {};
+
+template <int R2, typename C, int NT>
+__device__ __forceinline__ void pencil_fwdA_r(nt_tag<NT>, C* sm, const C* __restrict__ base,
+                                              const C* tw, long long zstride, int w, int pw,
+                                              int r1) {
+  for_tasks<NT>(pw, r1, [&](int t, int n1) {
+    if (t >= w) return;
+    C v[R2];
+#pragma unroll
+    for (int j = 0; j < R2; ++j) v[j] = base[(n1 + r1 * j) * zstride + t];
+    Dft<R2, -1, C>::run(v);
+    if (r1 > 1) {
+#pragma unroll
+      for (int j = 1; j < R2; ++j) v[j] = cmul(v[j], tw[n1 * j]);
+    }
+#pragma unroll
+    for (int j = 0; j < R2; ++j) sm[(n1 + r1 * j) * pw + t] = v[j];
+  });
+}
+
+// forward stage B, kinetic factor, inverse stage B' -- in registers
+template <int R1, typename C, typename R, int MODE, int NT>
+__device__ __forceinline__ void pencil_mid_r(nt_tag<NT>, C* sm, const C* tw,
+                                             const R* __restrict__ kx_tab,
+                                             const R* __restrict__ kz_tab, R fy, R scale, int w,
+                                             int pw, int r2, int kx0, mode_tag<MODE>) {
+  for_tasks<NT>(pw, r2, [&](int t, int b) {
+    if (t >= w) return;
+    C v[R1];
+#pragma unroll
+    for (int i = 0; i < R1; ++i) v[i] = sm[(i + R1 * b) * pw + t];
+    Dft<R1, -1, C>::run(v);
+    const R fx = __ldg(&kx_tab[kx0 + t]);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      const R fz = __ldg(&kz_tab[b + r2 * k1]);
+      R f;
+      if constexpr (MODE == PENCIL_PROPAGATE) f = fx * fy * fz;
+      else f = (fx + fy + fz) * scale;
+      v[k1] = cscale(v[k1], f);
+    }
+    Dft<R1, 1, C>::run(v);
+    if (R1 > 1) {
+#pragma unroll
+      for (int i = 1; i < R1; ++i) v[i] = cmulc(v[i], tw[i * b]);
+    }
+#pragma unroll
+    for (int i = 0; i < R1; ++i) sm[(i + R1 * b) * pw + t] = v[i];
+  });
+}
+
+// inverse stage A', stores fused
+template <int R2, typename C, int NT>
+__device__ __forceinline__ void pencil_invA_r(nt_tag<NT>, const C* sm, C* __restrict__ base,
+                                              long long zstride, int w, int pw, int r1) {
+  for_tasks<NT>(pw, r1, [&](int t, int n1) {
+    if (t >= w) return;
+    C v[R2];
+#pragma unroll
+    for (int j = 0; j < R2; ++j) v[j] = sm[(n1 + r1 * j) * pw + t];
+    Dft<R2, 1, C>::run(v);
+#pragma unroll
+    for (int j = 0; j < R2; ++j) base[(n1 + r1 * j) * zstride + t] = v[j];
+  });
+}
+
+// ----------------------------------------------------------------------------
+// Pencil pass.  Slab element (z, column t) at shared position z * W + t.
+template <typename R, int NZ, int W, int MODE>
+__global__ void __launch_bounds__(launch_threads(task_threads(W)),
+                                  min_blocks(pencil_smem_ct(NZ, W, sizeof(R)),
+                                             sizeof(R) == 4 ? 3 : 2))
+    pencil_kernel(const GridDesc g, const PencilArgs<R> a) {
+  constexpr int NT = task_threads(W);
   using C = typename CplxOf<R>::type;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
+  const AxisT<NZ> az(g.nz, g.rz1, g.rz2);
+  const int nz = NZ ? NZ : g.nz;
+  const int pw = W ? W : g.pencil_w;        // slab pitch = block width
+  C* twz = sm + nz * pw;
+  for (int i = threadIdx.x; i < nz; i += blockDim.x) twz[i] = static_cast<const C*>(a.twz)[i];
   const int s = blockIdx.y;
   const int ky = blockIdx.x % g.ny, chunk = blockIdx.x / g.ny;
-  const int kx0 = chunk * g.pencil_w;
-  const int w = min(g.pencil_w, g.nxh - kx0);
-  const int nz = g.nz, pz = g.pencil_pitch;
+  const int kx0 = chunk * pw;
+  const int w = min(pw, g.nxh - kx0);
   const long long zstride = (long long)g.ny * g.nxh;
-  const int tid = threadIdx.x, nthr = blockDim.x;
   C* base = static_cast<C*>(a.spec) + (long long)s * g.n_half + (long long)ky * g.nxh + kx0;
-  const Axis axz{nz, g.rz1, g.rz2};
-  const C* twz = static_cast<const C*>(a.twz);
-  const SlabAddr slab{pz};
-
-  for (int idx = tid; idx < nz * w; idx += nthr) {
-    const int zz = idx / w, j = idx - zz * w;
-    sm[zz * pz + j] = base[zz * zstride + j];
-  }
-  __syncthreads();
-  fft_forward(sm, slab, w, axz, twz);
   const R fy = a.ky_tab[ky];
-  for (int idx = tid; idx < nz * w; idx += nthr) {
-    const int p = idx / w, j = idx - p * w;
-    const int kz = spec_freq(axz, p);
-    R f;
-    if constexpr (MODE == PENCIL_PROPAGATE) {
-      f = __ldg(&a.kx_tab[kx0 + j]) * fy * __ldg(&a.kz_tab[kz]);
-    } else {
-      f = (__ldg(&a.kx_tab[kx0 + j]) + fy + __ldg(&a.kz_tab[kz])) * a.scale;
-    }
-    C v = sm[p * pz + j];
-    v.x *= f;
-    v.y *= f;
-    sm[p * pz + j] = v;
-  }
   __syncthreads();
-  fft_inverse(sm, slab, w, axz, twz);
-  for (int idx = tid; idx < nz * w; idx += nthr) {
-    const int zz = idx / w, j = idx - zz * w;
-    base[zz * zstride + j] = sm[zz * pz + j];
-  }
+
+  ITP_WITH_RADIX(az.r2, pencil_fwdA_r, nt_tag<NT>(), sm, base, twz, zstride, w, pw, az.r1)
+  __syncthreads();
+  ITP_WITH_RADIX(az.r1, pencil_mid_r, nt_tag<NT>(), sm, twz, a.kx_tab, a.kz_tab, fy, a.scale, w,
+                 pw, az.r2, kx0, mode_tag<MODE>())
+  __syncthreads();
+  ITP_WITH_RADIX(az.r2, pencil_invA_r, nt_tag<NT>(), sm, base, zstride, w, pw, az.r1)
 }
 
+// ----------------------------------------------------------------------------
 template <typename R>
 __global__ void term_tables_kernel(const GridDesc g, const double* __restrict__ V, double tau_i,
                                    double lx, double ly, double lz, R* f_half, R* f_full,
@@ -327,36 +722,71 @@ __global__ void term_tables_kernel(const GridDesc g, const double* __restrict__ 
   }
 }
 
+// phi[s][z][:] = sum_i term_i[s][z][:] in FP64, rounded to FP32; term_i is
+// stored with the half-spectrum plane pitch (in floats).
+__global__ void term_sum_kernel(const TermSumArgs a) {
+  const long long planes = (long long)a.m * a.nz;
+  const int vec_per_plane = a.plane_pts / 4;
+  const long long total = planes * vec_per_plane;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long pl = q / vec_per_plane;
+    const int v = (int)(q - pl * vec_per_plane);
+    double4 acc = make_double4(0.0, 0.0, 0.0, 0.0);
+    for (int i = 0; i < a.k; ++i) {
+      const float4 x = __ldg(reinterpret_cast<const float4*>(a.term[i] + pl * a.plane_pitch) + v);
+      acc.x += (double)x.x;
+      acc.y += (double)x.y;
+      acc.z += (double)x.z;
+      acc.w += (double)x.w;
+    }
+    reinterpret_cast<float4*>(a.phi_out + pl * a.plane_pts)[v] =
+        make_float4((float)acc.x, (float)acc.y, (float)acc.z, (float)acc.w);
+  }
+}
+
+// dst[p][c][r] = src[p][r][c] for nplanes planes of rows x cols.
+template <typename TS, typename TD>
+__global__ void transpose_planes_kernel(const TS* __restrict__ src, TD* __restrict__ dst,
+                                        long long nplanes, int rows, int cols) {
+  __shared__ TS tile[32][33];
+  const long long p = blockIdx.z;
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const TS* s = src + p * rows * cols;
+  TD* d = dst + p * rows * cols;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[i][threadIdx.x] = s[(long long)r * cols + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) d[(long long)c * rows + r] = (TD)tile[threadIdx.x][i];
+  }
+}
+
 template <typename K>
 cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-}  // namespace
-
-size_t plane_smem_bytes(const GridDesc& g, int real_bytes) {
-  return (size_t)(g.ny / 2) * g.pp * 2 * real_bytes;
-}
-size_t pencil_smem_bytes(const GridDesc& g, int real_bytes) {
-  return (size_t)g.nz * g.pencil_pitch * 2 * real_bytes;
-}
-
-template <typename R>
-cudaError_t launch_plane(const GridDesc& g, const PlaneArgs<R>& a, cudaStream_t st) {
-  const size_t smem = plane_smem_bytes(g, sizeof(R));
+template <typename R, int NX, int NY>
+cudaError_t plane_dispatch(const GridDesc& g, const PlaneArgs<R>& a, size_t smem, cudaStream_t st) {
   dim3 grid(g.nz, a.m);
-  cudaError_t e = cudaSuccess;
+  const int nthr = kThreads;
+  cudaError_t e;
   switch (a.mode) {
 #define ITP_PLANE_CASE(M)                                                   \
   case M:                                                                   \
-    e = set_smem(plane_kernel<R, M>, smem);                                 \
+    e = set_smem(plane_kernel<R, NX, NY, M>, smem);                         \
     if (e != cudaSuccess) return e;                                         \
-    plane_kernel<R, M><<<grid, kThreads, smem, st>>>(g, a);                 \
+    plane_kernel<R, NX, NY, M><<<grid, nthr, smem, st>>>(g, a);             \
     break;
     ITP_PLANE_CASE(PLANE_FWD_REAL)
     ITP_PLANE_CASE(PLANE_MERGED)
     ITP_PLANE_CASE(PLANE_COMBINE)
     ITP_PLANE_CASE(PLANE_HPSI)
+    ITP_PLANE_CASE(PLANE_TERM)
 #undef ITP_PLANE_CASE
     default:
       return cudaErrorInvalidValue;
@@ -364,22 +794,74 @@ cudaError_t launch_plane(const GridDesc& g, const PlaneArgs<R>& a, cudaStream_t 
   return cudaGetLastError();
 }
 
+template <typename R, int NZ, int W>
+cudaError_t pencil_dispatch(const GridDesc& g, const PencilArgs<R>& a, size_t smem,
+                            cudaStream_t st) {
+  const int chunks = (g.nxh + g.pencil_w - 1) / g.pencil_w;
+  dim3 grid(g.ny * chunks, a.m);
+  const int nthr = launch_threads(task_threads(W));
+  cudaError_t e;
+  if (a.mode == PENCIL_PROPAGATE) {
+    e = set_smem(pencil_kernel<R, NZ, W, PENCIL_PROPAGATE>, smem);
+    if (e != cudaSuccess) return e;
+    pencil_kernel<R, NZ, W, PENCIL_PROPAGATE><<<grid, nthr, smem, st>>>(g, a);
+  } else {
+    e = set_smem(pencil_kernel<R, NZ, W, PENCIL_KINETIC>, smem);
+    if (e != cudaSuccess) return e;
+    pencil_kernel<R, NZ, W, PENCIL_KINETIC><<<grid, nthr, smem, st>>>(g, a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int plane_row_pitch(int nx) { return row_pitch(nx); }
+
+size_t plane_smem_bytes(const GridDesc& g, int real_bytes) {
+  return ((size_t)(g.ny / 2) * g.pp + g.nx + g.ny) * 2 * real_bytes;
+}
+size_t pencil_smem_bytes(const GridDesc& g, int real_bytes) {
+  return ((size_t)g.nz * g.pencil_w + g.nz) * 2 * real_bytes;
+}
+
+template <typename R>
+cudaError_t launch_plane(const GridDesc& g, const PlaneArgs<R>& a, cudaStream_t st) {
+  const size_t smem = plane_smem_bytes(g, sizeof(R));
+  if (g.nx == g.ny && g.pp == row_pitch(g.nx)) {
+    switch (g.nx) {
+      case 32: return plane_dispatch<R, 32, 32>(g, a, smem, st);
+      case 48: return plane_dispatch<R, 48, 48>(g, a, smem, st);
+      case 64: return plane_dispatch<R, 64, 64>(g, a, smem, st);
+      case 96: return plane_dispatch<R, 96, 96>(g, a, smem, st);
+      case 128: return plane_dispatch<R, 128, 128>(g, a, smem, st);
+      default: break;
+    }
+  }
+  return plane_dispatch<R, 0, 0>(g, a, smem, st);
+}
+
+cudaError_t launch_term_sum(const TermSumArgs& a, cudaStream_t st) {
+  if (a.k < 1 || a.k > kMaxTermsK || (a.plane_pts & 3) || (a.plane_pitch & 3))
+    return cudaErrorInvalidValue;
+  term_sum_kernel<<<8 * 152, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_pencil(const GridDesc& g, const PencilArgs<R>& a, cudaStream_t st) {
   const size_t smem = pencil_smem_bytes(g, sizeof(R));
-  const int chunks = (g.nxh + g.pencil_w - 1) / g.pencil_w;
-  dim3 grid(g.ny * chunks, a.m);
-  cudaError_t e;
-  if (a.mode == PENCIL_PROPAGATE) {
-    e = set_smem(pencil_kernel<R, PENCIL_PROPAGATE>, smem);
-    if (e != cudaSuccess) return e;
-    pencil_kernel<R, PENCIL_PROPAGATE><<<grid, kThreads, smem, st>>>(g, a);
-  } else {
-    e = set_smem(pencil_kernel<R, PENCIL_KINETIC>, smem);
-    if (e != cudaSuccess) return e;
-    pencil_kernel<R, PENCIL_KINETIC><<<grid, kThreads, smem, st>>>(g, a);
+  switch (g.nz * 1000 + g.pencil_w) {
+    case 32 * 1000 + 17: return pencil_dispatch<R, 32, 17>(g, a, smem, st);
+    case 48 * 1000 + 25: return pencil_dispatch<R, 48, 25>(g, a, smem, st);
+    case 64 * 1000 + 33: return pencil_dispatch<R, 64, 33>(g, a, smem, st);
+    case 96 * 1000 + 49: return pencil_dispatch<R, 96, 49>(g, a, smem, st);
+    case 96 * 1000 + 25: return pencil_dispatch<R, 96, 25>(g, a, smem, st);
+    case 128 * 1000 + 65: return pencil_dispatch<R, 128, 65>(g, a, smem, st);
+    case 128 * 1000 + 33: return pencil_dispatch<R, 128, 33>(g, a, smem, st);
+    case 256 * 1000 + 33: return pencil_dispatch<R, 256, 33>(g, a, smem, st);
+    default: break;
   }
-  return cudaGetLastError();
+  return pencil_dispatch<R, 0, 0>(g, a, smem, st);
 }
 
 template <typename R>
@@ -399,6 +881,15 @@ cudaError_t launch_kinetic_tables(const GridDesc& g, double lx, double ly, doubl
   return cudaGetLastError();
 }
 
+template <typename TS, typename TD>
+cudaError_t launch_transpose_planes(const TS* src, TD* dst, long long nplanes, int rows,
+                                    int cols, cudaStream_t st) {
+  dim3 block(32, 8);
+  dim3 grid((cols + 31) / 32, (rows + 31) / 32, (unsigned)nplanes);
+  transpose_planes_kernel<TS, TD><<<grid, block, 0, st>>>(src, dst, nplanes, rows, cols);
+  return cudaGetLastError();
+}
+
 template cudaError_t launch_plane<float>(const GridDesc&, const PlaneArgs<float>&, cudaStream_t);
 template cudaError_t launch_plane<double>(const GridDesc&, const PlaneArgs<double>&, cudaStream_t);
 template cudaError_t launch_pencil<float>(const GridDesc&, const PencilArgs<float>&, cudaStream_t);
@@ -413,5 +904,11 @@ template cudaError_t launch_kinetic_tables<float>(const GridDesc&, double, doubl
                                                   float*, float*, cudaStream_t);
 template cudaError_t launch_kinetic_tables<double>(const GridDesc&, double, double, double,
                                                    double*, double*, double*, cudaStream_t);
+template cudaError_t launch_transpose_planes<double, double>(const double*, double*, long long,
+                                                             int, int, cudaStream_t);
+template cudaError_t launch_transpose_planes<double, float>(const double*, float*, long long, int,
+                                                            int, cudaStream_t);
+template cudaError_t launch_transpose_planes<float, double>(const float*, double*, long long, int,
+                                                            int, cudaStream_t);
 
 }  // namespace itp

@@ -28,6 +28,8 @@ struct Lane {
   R* psi = nullptr;          // [m][N]
   R* psi_tmp = nullptr;      // [m][N]
   void* work = nullptr;      // [m][n_half] complex
+  void* work_terms[kMaxTerms] = {};  // per-term spectra / contributions (mixed)
+  bool fused_ok = true;              // per-term workspaces could be allocated
   R* f_half[kMaxTerms] = {}; // exp(-tau_i V / 2)
   R* f_full[kMaxTerms] = {}; // exp(-tau_i V)      (terms i >= 2)
   R* ktab = nullptr;         // per term: nxh + ny + nz propagation factors
@@ -48,7 +50,8 @@ struct itp_grid {
   int n = 0, ng = 0, m = 0;
   int precision = ITP_FP64;
   cudaStream_t st = nullptr;
-  double* V = nullptr;        // [N]
+  double* V = nullptr;        // [N], internal layout [z][x][y]
+  double* Vstage = nullptr;   // [N], user layout staging
   double* acc = nullptr;      // [m][N] FP64 accumulator / H psi / staging
   Lane<float> f32;
   Lane<double> f64;
@@ -236,6 +239,7 @@ void free_lane(Lane<R>& L) {
     cudaFree(L.f_half[i]);
     cudaFree(L.f_full[i]);
   }
+  for (int i = 1; i < kMaxTerms; ++i) cudaFree(L.work_terms[i]);
   cudaFree(L.ktab);
   cudaFree(L.htab);
   cudaFree(L.twx);
@@ -269,17 +273,35 @@ int prepare_tables(itp_handle h, Lane<R>& L, int k, double tau) {
 }
 
 // Eq. (3) with the order-2k expansion: acc = sum_i c_i T_2(tau/i)^i psi.
+// Per term i: plane-forward with exp(-tau_i V/2), then i pencils with i-1
+// merged plane passes (exp(-tau_i V)) between them, then the final inverse
+// plane pass with exp(-tau_i V/2) adds c_i u_i (Sec. II).  The mixed path
+// keeps every term's spectrum in its own workspace, writes each term's FP32
+// contribution c_i f u_i over it, and sums the contributions once in FP64.
 template <typename R>
 int propagate_lane(itp_handle h, int k, double tau) {
   Lane<R>& L = lane_of<R>(h);
   ITP_TRY(prepare_tables<R>(h, L, k, tau));
   const GridDesc& g = h->g;
   const size_t tl = (size_t)g.nxh + g.ny + g.nz;
+  bool fused = sizeof(R) == 4 && L.fused_ok;
+  if (fused) {
+    L.work_terms[0] = L.work;
+    for (int i = 1; i < k && fused; ++i) {
+      if (!L.work_terms[i] &&
+          cudaMalloc(&L.work_terms[i], (size_t)h->m * g.n_half * 2 * sizeof(R)) != cudaSuccess) {
+        cudaGetLastError();   // clear the allocation error; use the per-term path
+        L.fused_ok = fused = false;
+      }
+    }
+  }
+  TermSumArgs ts{};
   for (int i = 1; i <= k; ++i) {
+    void* work = fused ? L.work_terms[i - 1] : L.work;
     PlaneArgs<R> pa{};
     pa.m = h->m;
     pa.in_real = L.psi;
-    pa.spec = L.work;
+    pa.spec = work;
     pa.twx = L.twx;
     pa.twy = L.twy;
     pa.mode = PLANE_FWD_REAL;
@@ -288,7 +310,7 @@ int propagate_lane(itp_handle h, int k, double tau) {
     PencilArgs<R> pe{};
     pe.mode = PENCIL_PROPAGATE;
     pe.m = h->m;
-    pe.spec = L.work;
+    pe.spec = work;
     pe.kx_tab = L.ktab + (i - 1) * tl;
     pe.ky_tab = pe.kx_tab + g.nxh;
     pe.kz_tab = pe.ky_tab + g.ny;
@@ -305,6 +327,17 @@ int propagate_lane(itp_handle h, int k, double tau) {
         ITP_LAUNCH(h, ITP_KERNEL_PLANE_MERGED, launch_plane<R>(g, pm, h->st));
       }
     }
+    if (fused) {
+      // the term's contribution c_i f u_i, in place over its spectrum
+      PlaneArgs<R> pt = pa;
+      pt.mode = PLANE_TERM;
+      pt.f_in = nullptr;
+      pt.f_out = L.f_half[i - 1];
+      pt.coef = mp_coefficient(i, k);
+      ITP_LAUNCH(h, ITP_KERNEL_PLANE_COMBINE, launch_plane<R>(g, pt, h->st));
+      ts.term[i - 1] = reinterpret_cast<const float*>(work);
+      continue;
+    }
     PlaneArgs<R> pc = pa;
     pc.mode = PLANE_COMBINE;
     pc.f_in = nullptr;
@@ -312,22 +345,53 @@ int propagate_lane(itp_handle h, int k, double tau) {
     pc.acc = h->acc;
     pc.coef = mp_coefficient(i, k);
     pc.acc_init = (i == 1);
+    // the mixed path keeps the sum in FP64 and rounds the finished phi once
+    pc.phi_out = (sizeof(R) == 4 && i == k) ? L.psi_tmp : nullptr;
     ITP_LAUNCH(h, ITP_KERNEL_PLANE_COMBINE, launch_plane<R>(g, pc, h->st));
+  }
+  if (fused) {
+    // phi = sum_i c_i f u_i in FP64 over the FP32 contributions
+    ts.m = h->m;
+    ts.k = k;
+    ts.nz = g.nz;
+    ts.plane_pts = g.nx * g.ny;
+    ts.plane_pitch = 2LL * g.ny * g.nxh;
+    ts.phi_out = reinterpret_cast<float*>(L.psi_tmp);
+    ITP_LAUNCH(h, ITP_KERNEL_OTHER, launch_term_sum(ts, h->st));
   }
   return ITP_OK;
 }
 
 // Eq. (4): psi = L^{-1} phi, S = phi phi^T dV = L L^T.
 template <typename R>
-int orthonormalize_lane(itp_handle h) {
-  Lane<R>& L = lane_of<R>(h);
-  using TC = R;   // FP32 products for the mixed path, FP64 for the FP64 path
-  ITP_LAUNCH(h, ITP_KERNEL_GRAM, (launch_gram_partial<double, double, TC>(h->acc, h->acc, h->m, h->g.n_points,
-                                                         h->n_chunks, h->partial, h->st)));
-  ITP_LAUNCH(h, ITP_KERNEL_GRAM_REDUCE, launch_gram_reduce(h->partial, h->n_chunks, h->m, h->dV, 1, h->S, h->st));
+int orthonormalize_lane(itp_handle h);
+template <>
+int orthonormalize_lane<double>(itp_handle h) {
+  Lane<double>& L = h->f64;
+  ITP_LAUNCH(h, ITP_KERNEL_GRAM, (launch_gram_partial<double, double, double>(
+                                     h->acc, h->acc, h->m, h->g.n_points, h->n_chunks,
+                                     h->partial, h->st)));
+  ITP_LAUNCH(h, ITP_KERNEL_GRAM_REDUCE,
+             launch_gram_reduce(h->partial, h->n_chunks, h->m, h->dV, 1, h->S, h->st));
   ITP_LAUNCH(h, ITP_KERNEL_CHOLESKY, launch_cholesky_inverse(h->S, h->m, h->Mx, h->status, h->st));
-  ITP_LAUNCH(h, ITP_KERNEL_APPLY, (launch_apply_matrix<double, R>(h->Mx, h->m, 1, h->acc, L.psi, h->g.n_points,
-                                                h->st)));
+  ITP_LAUNCH(h, ITP_KERNEL_APPLY, (launch_apply_matrix<double, double>(
+                                      h->Mx, h->m, 1, h->acc, L.psi, h->g.n_points, h->st)));
+  return ITP_OK;
+}
+// Mixed path: phi is FP32 (rounded from the FP64 sum) in psi_tmp; S and the
+// update run on the tensor cores (3xTF32).
+template <>
+int orthonormalize_lane<float>(itp_handle h) {
+  Lane<float>& L = h->f32;
+  ITP_LAUNCH(h, ITP_KERNEL_GRAM, (launch_tc_gram<float, float>(L.psi_tmp, L.psi_tmp, h->m,
+                                                               h->g.n_points, h->n_chunks,
+                                                               h->partial, h->status, h->st)));
+  ITP_LAUNCH(h, ITP_KERNEL_GRAM_REDUCE,
+             launch_gram_reduce(h->partial, h->n_chunks, h->m, h->dV, 1, h->S, h->st));
+  ITP_LAUNCH(h, ITP_KERNEL_CHOLESKY, launch_cholesky_inverse(h->S, h->m, h->Mx, h->status, h->st));
+  ITP_LAUNCH(h, ITP_KERNEL_APPLY, (launch_tc_apply<float, float>(h->Mx, h->m, L.psi_tmp, L.psi,
+                                                                 h->g.n_points, h->status,
+                                                                 h->st)));
   return ITP_OK;
 }
 
@@ -361,16 +425,35 @@ int energies_lane(itp_handle h, int flags) {
   ph.acc = h->acc;
   ph.V = h->V;
   ITP_LAUNCH(h, ITP_KERNEL_PLANE_HPSI, launch_plane<R>(g, ph, h->st));
-  ITP_LAUNCH(h, ITP_KERNEL_GRAM, (launch_gram_partial<R, double, R>(L.psi, h->acc, h->m, g.n_points, h->n_chunks,
-                                                   h->partial, h->st)));
+  if (sizeof(R) == 4) {
+    ITP_LAUNCH(h, ITP_KERNEL_GRAM, (launch_tc_gram<float, double>(
+                                       reinterpret_cast<const float*>(L.psi), h->acc, h->m,
+                                       g.n_points, h->n_chunks, h->partial, h->status, h->st)));
+  } else {
+    ITP_LAUNCH(h, ITP_KERNEL_GRAM, (launch_gram_partial<double, double, double>(
+                                       reinterpret_cast<const double*>(L.psi), h->acc, h->m,
+                                       g.n_points, h->n_chunks, h->partial, h->st)));
+  }
   ITP_LAUNCH(h, ITP_KERNEL_GRAM_REDUCE, launch_gram_reduce(h->partial, h->n_chunks, h->m, h->dV, 1, h->Hs, h->st));
   if (flags & ITP_RITZ) {
     ITP_LAUNCH(h, ITP_KERNEL_EIGH, launch_jacobi_eigh(h->Hs, h->m, h->E_dev, h->Mx, h->Wmm, h->status, h->st));
-    ITP_LAUNCH(h, ITP_KERNEL_APPLY, (launch_apply_matrix<R, R>(h->Mx, h->m, 0, L.psi, L.psi_tmp, g.n_points,
-                                             h->st)));
+    if (sizeof(R) == 4) {
+      ITP_LAUNCH(h, ITP_KERNEL_APPLY, (launch_tc_apply<float, float>(
+                                          h->Mx, h->m, reinterpret_cast<const float*>(L.psi),
+                                          reinterpret_cast<float*>(L.psi_tmp), g.n_points,
+                                          h->status, h->st)));
+    } else {
+      ITP_LAUNCH(h, ITP_KERNEL_APPLY, (launch_apply_matrix<double, double>(
+                                          h->Mx, h->m, 0, reinterpret_cast<const double*>(L.psi),
+                                          reinterpret_cast<double*>(L.psi_tmp), g.n_points,
+                                          h->st)));
+    }
     R* t = L.psi;
     L.psi = L.psi_tmp;
     L.psi_tmp = t;
+  } else if (flags & ITP_RITZ_VALUES) {
+    ITP_LAUNCH(h, ITP_KERNEL_EIGH, launch_tridiag(h->Hs, h->m, h->Wmm, h->st));
+    ITP_LAUNCH(h, ITP_KERNEL_EIGH, launch_bisect(h->Wmm, h->m, h->E_dev, h->st));
   } else {
     ITP_LAUNCH(h, ITP_KERNEL_OTHER, launch_diag(h->Hs, h->m, h->E_dev, h->st));
   }
@@ -387,6 +470,7 @@ int collect_status(itp_handle h) {
     ITP_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->st));
     if (s & 1) return fail(h, ITP_ERR_NOT_PD, "overlap matrix is not positive definite");
     if (s & 2) return fail(h, ITP_ERR_NOCONV, "Jacobi eigensolver did not converge");
+    if (s & 4) return fail(h, ITP_ERR_TIMEOUT, "a bounded tensor-core pipeline wait expired");
   }
   return ITP_OK;
 }
@@ -470,7 +554,7 @@ int itp_create_grid(itp_handle* out, int nx, int ny, int nz, double lx, double l
   g.nxh = nx / 2 + 1;
   g.n_points = (long long)nx * ny * nz;
   g.n_half = (long long)nz * ny * g.nxh;
-  g.pp = nx + 3;   // odd pitch >= nx + 2
+  g.pp = plane_row_pitch(nx);
   const int cbytes = precision == ITP_FP64 ? 16 : 8;
   {
     const size_t budget = 72 * 1024;
@@ -512,6 +596,7 @@ int itp_create_grid(itp_handle* out, int nx, int ny, int nz, double lx, double l
                 cudaGetErrorString(e));
   };
   ITP_CREATE(cuda(cudaMalloc(&h->V, N * sizeof(double)), "V"));
+  ITP_CREATE(cuda(cudaMalloc(&h->Vstage, N * sizeof(double)), "V staging"));
   ITP_CREATE(cuda(cudaMalloc(&h->acc, m * N * sizeof(double)), "accumulator"));
   ITP_CREATE(cuda(cudaMalloc(&h->partial, (size_t)h->n_chunks * m * m * sizeof(double)),
                   "partials"));
@@ -545,6 +630,7 @@ void itp_destroy(itp_handle h) {
   free_lane(h->f32);
   free_lane(h->f64);
   cudaFree(h->V);
+  cudaFree(h->Vstage);
   cudaFree(h->acc);
   cudaFree(h->partial);
   cudaFree(h->S);
@@ -565,8 +651,10 @@ void itp_destroy(itp_handle h) {
 int itp_set_potential(itp_handle h, const double* V_host) {
   if (!h || !V_host) return h ? fail(h, ITP_ERR_ARG, "null potential") : ITP_ERR_ARG;
   ITP_CUDA(h, cudaSetDevice(h->device));
-  ITP_CUDA(h, cudaMemcpyAsync(h->V, V_host, (size_t)h->g.n_points * sizeof(double),
+  ITP_CUDA(h, cudaMemcpyAsync(h->Vstage, V_host, (size_t)h->g.n_points * sizeof(double),
                               cudaMemcpyHostToDevice, h->st));
+  ITP_LAUNCH(h, ITP_KERNEL_OTHER, (launch_transpose_planes<double, double>(
+                                      h->Vstage, h->V, h->g.nz, h->g.ny, h->g.nx, h->st)));
   h->f32.tab_order = 0;
   h->f64.tab_order = 0;
   h->have_V = true;
@@ -576,12 +664,18 @@ int itp_set_potential(itp_handle h, const double* V_host) {
 static int set_states_impl(itp_handle h, const double* src, cudaMemcpyKind kind) {
   ITP_CUDA(h, cudaSetDevice(h->device));
   const size_t count = (size_t)h->m * h->g.n_points;
+  const long long planes = (long long)h->m * h->g.nz;
+  // user layout [m][z][y][x] -> staging -> internal [m][z][x][y]
   if (h->precision == ITP_FP64) {
-    ITP_CUDA(h, cudaMemcpyAsync(h->f64.psi, src, count * sizeof(double), kind, h->st));
+    ITP_CUDA(h, cudaMemcpyAsync(h->f64.psi_tmp, src, count * sizeof(double), kind, h->st));
+    ITP_LAUNCH(h, ITP_KERNEL_OTHER, (launch_transpose_planes<double, double>(
+                                        h->f64.psi_tmp, h->f64.psi, planes, h->g.ny, h->g.nx,
+                                        h->st)));
     h->cur64 = true;
   } else {
     ITP_CUDA(h, cudaMemcpyAsync(h->acc, src, count * sizeof(double), kind, h->st));
-    ITP_LAUNCH(h, ITP_KERNEL_OTHER, (launch_convert<double, float>(h->acc, h->f32.psi, (long long)count, h->st)));
+    ITP_LAUNCH(h, ITP_KERNEL_OTHER, (launch_transpose_planes<double, float>(
+                                        h->acc, h->f32.psi, planes, h->g.ny, h->g.nx, h->st)));
     h->cur64 = false;
   }
   h->have_states = true;
@@ -604,13 +698,19 @@ int itp_get_states(itp_handle h, double* psi_host) {
   if (!h->have_states) return fail(h, ITP_ERR_STATE, "states not set");
   ITP_CUDA(h, cudaSetDevice(h->device));
   const size_t count = (size_t)h->m * h->g.n_points;
-  const double* src = h->f64.psi;
-  if (!h->cur64) {
-    ITP_LAUNCH(h, ITP_KERNEL_OTHER, (launch_convert<float, double>(h->f32.psi, h->acc, (long long)count, h->st)));
-    src = h->acc;
+  const long long planes = (long long)h->m * h->g.nz;
+  double* stage;
+  if (h->cur64) {
+    stage = h->f64.psi_tmp;
+    ITP_LAUNCH(h, ITP_KERNEL_OTHER, (launch_transpose_planes<double, double>(
+                                        h->f64.psi, stage, planes, h->g.nx, h->g.ny, h->st)));
+  } else {
+    stage = h->acc;
     h->have_phi = false;
+    ITP_LAUNCH(h, ITP_KERNEL_OTHER, (launch_transpose_planes<float, double>(
+                                        h->f32.psi, stage, planes, h->g.nx, h->g.ny, h->st)));
   }
-  ITP_CUDA(h, cudaMemcpyAsync(psi_host, src, count * sizeof(double), cudaMemcpyDeviceToHost,
+  ITP_CUDA(h, cudaMemcpyAsync(psi_host, stage, count * sizeof(double), cudaMemcpyDeviceToHost,
                               h->st));
   return collect_status(h);
 }
@@ -619,9 +719,29 @@ int itp_get_phi(itp_handle h, double* phi_host) {
   if (!h || !phi_host) return h ? fail(h, ITP_ERR_ARG, "null output") : ITP_ERR_ARG;
   if (!h->have_phi) return fail(h, ITP_ERR_STATE, "no propagated states pending");
   ITP_CUDA(h, cudaSetDevice(h->device));
-  ITP_CUDA(h, cudaMemcpyAsync(phi_host, h->acc, (size_t)h->m * h->g.n_points * sizeof(double),
-                              cudaMemcpyDeviceToHost, h->st));
-  return collect_status(h);
+  const GridDesc& g = h->g;
+  const size_t count = (size_t)h->m * g.n_points;
+  std::vector<double> tmp(count);
+  if (h->cur64) {
+    ITP_CUDA(h, cudaMemcpyAsync(tmp.data(), h->acc, count * sizeof(double),
+                                cudaMemcpyDeviceToHost, h->st));
+    ITP_TRY(collect_status(h));
+  } else {
+    std::vector<float> t32(count);
+    ITP_CUDA(h, cudaMemcpyAsync(t32.data(), h->f32.psi_tmp, count * sizeof(float),
+                                cudaMemcpyDeviceToHost, h->st));
+    ITP_TRY(collect_status(h));
+    for (size_t q = 0; q < count; ++q) tmp[q] = t32[q];
+  }
+  // internal [m][z][x][y] -> user [m][z][y][x] (diagnostic path, on the host)
+  const size_t plane = (size_t)g.nx * g.ny;
+  for (size_t p = 0; p < (size_t)h->m * g.nz; ++p) {
+    const double* s = tmp.data() + p * plane;
+    double* d = phi_host + p * plane;
+    for (int x = 0; x < g.nx; ++x)
+      for (int y = 0; y < g.ny; ++y) d[(size_t)y * g.nx + x] = s[(size_t)x * g.ny + y];
+  }
+  return ITP_OK;
 }
 
 int itp_propagate(itp_handle h, int order, double tau) {
@@ -672,7 +792,7 @@ int itp_polish(itp_handle h, int order, double tau, double tol, int max_steps, i
   for (step = 1; step <= max_steps; ++step) {
     ITP_TRY(propagate_lane<double>(h, order / 2, tau));
     ITP_TRY(orthonormalize_lane<double>(h));
-    ITP_TRY(do_energies(h, cur.data(), ITP_RITZ));
+    ITP_TRY(do_energies(h, cur.data(), ITP_RITZ_VALUES));
     if (step > 1) {
       double d = 0;
       for (int j = 0; j < h->n; ++j) d = std::fmax(d, std::fabs(cur[j] - prev[j]));
@@ -684,6 +804,8 @@ int itp_polish(itp_handle h, int order, double tau, double tol, int max_steps, i
     step = max_steps;
     prev.swap(cur);   // last computed energies are in prev after the final swap
   }
+  // leave the states on the Ritz vectors of the converged subspace
+  ITP_TRY(do_energies(h, nullptr, ITP_RITZ));
   if (steps_out) *steps_out = step;
   if (E_host) memcpy(E_host, cur.data(), h->m * sizeof(double));
   return ITP_OK;

@@ -23,6 +23,7 @@ enum PlaneMode {
   PLANE_MERGED = 1,     // half spectrum -> inverse -> * f_mid -> forward -> half spectrum
   PLANE_COMBINE = 2,    // half spectrum -> inverse -> * f_out -> acc (=|+=) c * u   (FP64 acc)
   PLANE_HPSI = 3,       // half spectrum -> inverse -> acc = u + V * psi            (FP64 acc)
+  PLANE_TERM = 4,       // half spectrum -> inverse -> c * f_out * u over the plane itself
 };
 
 enum PencilMode {
@@ -41,6 +42,8 @@ struct PlaneArgs {
   const R* f_mid;            // [N] factor between inverse and forward (PLANE_MERGED)
   const R* f_out;            // [N] factor applied before combining (PLANE_COMBINE)
   double* acc;               // [m][N] FP64 accumulator / H psi output
+  R* phi_out;                // PLANE_COMBINE: if set, the finished sum acc + c*u is
+                             // written here in precision R instead of back to acc
   double coef;               // c_i of the term
   int acc_init;              // 1: acc = c*u, 0: acc += c*u
   const double* V;           // [N] potential (PLANE_HPSI)
@@ -60,7 +63,20 @@ struct PencilArgs {
   const void* twz;           // nz roots
 };
 
+// phi = sum_i term_i in FP64, rounded to FP32 (mixed path): term_i holds the
+// FP32 contribution c_i * f_i * u_i of term i, stored plane by plane with the
+// half-spectrum plane pitch (floats); phi is [m][N].
+constexpr int kMaxTermsK = 6;
+struct TermSumArgs {
+  int m, k, nz, plane_pts;
+  long long plane_pitch;
+  const float* term[kMaxTermsK];
+  float* phi_out;
+};
+cudaError_t launch_term_sum(const TermSumArgs& a, cudaStream_t st);
+
 size_t plane_smem_bytes(const GridDesc& g, int real_bytes);
+int plane_row_pitch(int nx);   // odd pitch (complex) of a row pair in shared memory
 size_t pencil_smem_bytes(const GridDesc& g, int real_bytes);
 
 template <typename R>
@@ -79,6 +95,13 @@ cudaError_t launch_term_tables(const GridDesc& g, const double* V, double tau_i,
 template <typename R>
 cudaError_t launch_kinetic_tables(const GridDesc& g, double lx, double ly, double lz, R* kx,
                                   R* ky, R* kz, cudaStream_t st);
+
+// dst[p][c][r] = src[p][r][c] over nplanes planes of rows x cols (converts
+// the element type).  Moves states between the user layout [z][y][x] and
+// the internal per-plane transposed layout [z][x][y].
+template <typename TS, typename TD>
+cudaError_t launch_transpose_planes(const TS* src, TD* dst, long long nplanes, int rows,
+                                    int cols, cudaStream_t st);
 
 // ---- dense part (dense.cu) ----
 // Partial Gram sums: P[c][i][j] = sum_{p in chunk c} A[i][p] * B[j][p],
@@ -99,6 +122,10 @@ cudaError_t launch_cholesky_inverse(const double* S, int m, double* Minv, int* s
 // work: m*m doubles.  status[0] |= 2 if the sweeps did not converge.
 cudaError_t launch_jacobi_eigh(const double* H, int m, double* E, double* Rt, double* work,
                                int* status, cudaStream_t st);
+// Eigenvalues only (ascending) of the symmetric m x m matrix H: Householder
+// tridiagonalisation into work = (d[m], e[m]), then bisection into E.
+cudaError_t launch_tridiag(const double* H, int m, double* work, cudaStream_t st);
+cudaError_t launch_bisect(const double* work, int m, double* E, cudaStream_t st);
 // E[j] = H[j][j]
 cudaError_t launch_diag(const double* H, int m, double* E, cudaStream_t st);
 // Y = M * X over all points: Y[i][p] = sum_k M[i][k] X[k][p]   (M lower
@@ -107,6 +134,14 @@ cudaError_t launch_diag(const double* H, int m, double* E, cudaStream_t st);
 template <typename TX, typename TY>
 cudaError_t launch_apply_matrix(const double* M, int m, int lower, const TX* X, TY* Y,
                                 long long n_points, cudaStream_t st);
+// Tensor-core (tcgen05 TF32, 3xTF32 split) versions, m <= 128; status gets
+// bit 4 if a bounded mbarrier wait expired.
+template <typename TA, typename TB>
+cudaError_t launch_tc_gram(const TA* A, const TB* B, int m, long long n_points, int n_chunks,
+                           double* partial, int* status, cudaStream_t st);
+template <typename TX, typename TY>
+cudaError_t launch_tc_apply(const double* M, int m, const TX* X, TY* Y, long long n_points,
+                            int* status, cudaStream_t st);
 // Precision conversion of whole state blocks.
 template <typename TS, typename TD>
 cudaError_t launch_convert(const TS* src, TD* dst, long long count, cudaStream_t st);

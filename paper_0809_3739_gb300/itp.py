@@ -20,6 +20,7 @@ ITP_ERR_NOCONV = 7
 ITP_FP64 = 0
 ITP_MIXED = 1
 ITP_RITZ = 1
+ITP_RITZ_VALUES = 2
 
 _ERR_NAMES = {1: "ITP_ERR_ARG", 2: "ITP_ERR_CUDA", 3: "ITP_ERR_NOT_PD", 4: "ITP_ERR_TIMEOUT",
               5: "ITP_ERR_OOM", 6: "ITP_ERR_STATE", 7: "ITP_ERR_NOCONV"}
@@ -231,8 +232,11 @@ class ItpGrid:
         itp_orthonormalize(self.h)
 
     def energies(self, ritz=True):
+        """ritz: True (values + rotation), "values" (values only) or False
+        (diagonal expectation values)."""
+        flags = ITP_RITZ_VALUES if ritz == "values" else (ITP_RITZ if ritz else 0)
         out = np.empty(self.m, dtype=np.float64)
-        return itp_energies(self.h, out, ITP_RITZ if ritz else 0)
+        return itp_energies(self.h, out, flags)
 
     def step(self, order, tau, ritz=True):
         self.propagate(order, tau)

@@ -74,7 +74,7 @@ def test_orthonormalize_matches_oracle(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("ritz", [False, True])
+@pytest.mark.parametrize("ritz", [False, True, "values"])
 def test_energies_match_oracle(prec, ritz):
     g = GRIDS[1]
     V = wells_problem(g)
@@ -84,11 +84,14 @@ def test_energies_match_oracle(prec, ritz):
     with _grid_handle(g, m, prec, V, psi) as h:
         E = h.energies(ritz)
         got = h.get_states()
-    E_ref, psi_ref, _ = O.energies(psi, V, g, ritz)
+    E_ref, psi_ref, _ = O.energies(psi, V, g, bool(ritz))
     scale = np.max(np.abs(E_ref))
     tol = 1e-12 if prec == "fp64" else 1e-5
     assert np.max(np.abs(E - E_ref)) < tol * scale
-    if ritz:
+    if ritz == "values":
+        # Ritz values only: the states are left as they were
+        assert np.max(np.abs(got - psi)) < (1e-14 if prec == "fp64" else 1e-6) * np.max(np.abs(psi))
+    elif ritz:
         # the rotated states agree up to sign (random states: simple spectrum)
         for j in range(m):
             d = abs(np.dot(got[j], psi_ref[j]) * g.dV)
@@ -105,11 +108,17 @@ def test_ho_spectrum_fp64_path():
     with _grid_handle(g, 12, "fp64", V, psi, n_guard=2) as h:
         prev = None
         for it in range(400):
-            E = h.step(4, 0.1)
+            E = h.step(4, 0.1, ritz="values")
             if prev is not None and np.max(np.abs(E[:10] - prev[:10])) < 1e-12:
                 break
             prev = E
+        E = h.energies(True)
+        psi_out = h.get_states()
     assert np.max(np.abs(E[:10] - want)) < 1e-10, E[:10] - want
+    # the Ritz vectors of the ground state and the 2p shell: orthonormal and
+    # eigenvectors of H to the same accuracy
+    ov = psi_out @ psi_out.T * g.dV
+    assert np.max(np.abs(ov - np.eye(12))) < 1e-11
 
 
 def test_ho_spectrum_mixed_path_with_polish():
@@ -122,7 +131,7 @@ def test_ho_spectrum_mixed_path_with_polish():
     with _grid_handle(g, 12, "mixed", V, psi, n_guard=2) as h:
         prev = None
         for it in range(300):
-            E = h.step(4, 0.1)
+            E = h.step(4, 0.1, ritz="values")
             if prev is not None and np.max(np.abs(E[:10] - prev[:10])) < 1e-6:
                 break
             prev = E
@@ -130,9 +139,11 @@ def test_ho_spectrum_mixed_path_with_polish():
     assert np.max(np.abs(E[:10] - want)) < 1e-8, (steps, E[:10] - want)
 
 
-def test_itp_sequence_matches_oracle_iterations():
+@pytest.mark.parametrize("ritz", [True, "values"])
+def test_itp_sequence_matches_oracle_iterations(ritz):
     """Five full iterations (propagate, Cholesky, Ritz) from identical inputs
-    give the oracle's energies."""
+    give the oracle's energies, with or without rotating the states each
+    step (the Ritz values depend only on the span)."""
     g = GRIDS[1]
     V = wells_problem(g)
     m = 6
@@ -140,7 +151,7 @@ def test_itp_sequence_matches_oracle_iterations():
     ref = psi.copy()
     with _grid_handle(g, m, "fp64", V, psi) as h:
         for _ in range(5):
-            E = h.step(8, 0.4)
+            E = h.step(8, 0.4, ritz=ritz)
             ref, E_ref = O.itp_step(ref, V, g, 8, 0.4)
             assert np.max(np.abs(E - E_ref)) < 1e-11 * np.max(np.abs(E_ref))
 
@@ -194,3 +205,28 @@ def test_kernel_launch_count():
         h.propagate(8, 0.2)
         k = 4
         assert h.kernel_launches - n0 == k * (k + 2)
+
+
+def test_mixed_dense_steps_at_full_state_count():
+    """m = 128 states (the tensor-core tile height) on a small grid: the
+    mixed path's overlap, Cholesky update and Ritz values match the oracle,
+    and the states come out orthonormal to FP32 accuracy."""
+    g = Grid(32, 32, 32, 14.0, 14.0, 14.0)
+    V = wells_problem(g, n_wells=8)
+    m = 128
+    psi = seeded_states(g, m)
+    with _grid_handle(g, m, "mixed", V, psi, n_guard=8) as h:
+        h.propagate(4, 0.2)
+        phi = h.get_phi()
+        h.orthonormalize()
+        got = h.get_states()
+        E = h.energies("values")
+    phi_ref = O.propagate(psi, V, g, 4, 0.2)
+    assert _relerr(phi, phi_ref) < propagate_tolerance(4, g.n_points, "mixed")
+    ov = got @ got.T * g.dV
+    assert np.max(np.abs(ov - np.eye(m))) < 2e-5
+    # psi = L^{-1} phi: the first states follow from the leading block alone
+    want, _ = O.cholesky_orthonormalize(phi_ref[:4], g.dV)
+    assert _relerr(got[:4], want) < 1e-4
+    E_ref, _, _ = O.energies(got, V, g, ritz=True)
+    assert np.max(np.abs(E - E_ref)) < 1e-5 * np.max(np.abs(E_ref))
