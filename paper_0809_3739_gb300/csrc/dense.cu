@@ -594,5 +594,6 @@ template cudaError_t launch_apply_matrix<float, float>(const double*, int, int, 
                                                        float*, long long, cudaStream_t);
 template cudaError_t launch_convert<float, double>(const float*, double*, long long, cudaStream_t);
 template cudaError_t launch_convert<double, float>(const double*, float*, long long, cudaStream_t);
+template cudaError_t launch_convert<double, double>(const double*, double*, long long, cudaStream_t);
 
 }  // namespace itp

@@ -474,40 +474,51 @@ struct EpiTerm {
   using C = typename CplxOf<R>::type;
   const C* f;
   C* out;
-  double c;
+  R c;   // c_i rounded to R: the term is an R value anyway
   int npair, r1;
   template <int R2> __device__ __forceinline__ bool apply(int t, int n1, C* a) const {
 #pragma unroll
     for (int j = 0; j < R2; ++j) {
       const int idx = (n1 + r1 * j) * npair + t;
-      const C u = cmulri(a[j], __ldg(&f[idx]));
+      const C fv = __ldg(&f[idx]);
       C w;
-      w.x = (R)(c * (double)u.x);
-      w.y = (R)(c * (double)u.y);
+      w.x = c * (a[j].x * fv.x);
+      w.y = c * (a[j].y * fv.y);
       out[idx] = w;
     }
     return false;
   }
 };
 
-// PLANE_HPSI: out = u + V * psi in FP64.
+// PLANE_HPSI: out = u + V * psi, in FP64 (out64) or in R (outr, with the
+// potential in R: the mixed path's subspace matrix is formed from FP32 data).
 template <typename R>
 struct EpiHpsi {
   using C = typename CplxOf<R>::type;
   const C* psi;
   const double2* V;
   double2* out;
+  const C* Vr;
+  C* outr;
   int npair, r1;
   template <int R2> __device__ __forceinline__ bool apply(int t, int n1, C* a) const {
 #pragma unroll
     for (int j = 0; j < R2; ++j) {
       const int idx = (n1 + r1 * j) * npair + t;
       const C q = psi[idx];
-      const double2 v = __ldg(&V[idx]);
-      double2 h;
-      h.x = (double)a[j].x + v.x * (double)q.x;
-      h.y = (double)a[j].y + v.y * (double)q.y;
-      out[idx] = h;
+      if (outr) {
+        const C v = __ldg(&Vr[idx]);
+        C h;
+        h.x = a[j].x + v.x * q.x;
+        h.y = a[j].y + v.y * q.y;
+        outr[idx] = h;
+      } else {
+        const double2 v = __ldg(&V[idx]);
+        double2 h;
+        h.x = (double)a[j].x + v.x * (double)q.x;
+        h.y = (double)a[j].y + v.y * (double)q.y;
+        out[idx] = h;
+      }
     }
     return false;
   }
@@ -555,7 +566,7 @@ __global__ void __launch_bounds__(launch_threads(PlaneGeo<R, NX, NY>::NT),
       __syncthreads();
     } else if constexpr (MODE == PLANE_TERM) {
       EpiTerm<R> epi{reinterpret_cast<const C*>(a.f_out + fac_off),
-                     static_cast<C*>(a.spec) + spec_off, a.coef, G.npair, G.ax.r1};
+                     static_cast<C*>(a.spec) + spec_off, (R)a.coef, G.npair, G.ax.r1};
       xA_inv_then(G, sm, twx, epi);
       return;
     } else if constexpr (MODE == PLANE_COMBINE) {
@@ -568,7 +579,10 @@ __global__ void __launch_bounds__(launch_threads(PlaneGeo<R, NX, NY>::NT),
     } else {
       EpiHpsi<R> epi{reinterpret_cast<const C*>(a.in_real + real_off),
                      reinterpret_cast<const double2*>(a.V + fac_off),
-                     reinterpret_cast<double2*>(a.acc + real_off), G.npair, G.ax.r1};
+                     reinterpret_cast<double2*>(a.acc + real_off),
+                     a.V_r ? reinterpret_cast<const C*>(a.V_r + fac_off) : nullptr,
+                     a.phi_out ? reinterpret_cast<C*>(a.phi_out + real_off) : nullptr,
+                     G.npair, G.ax.r1};
       xA_inv_then(G, sm, twx, epi);
       return;
     }
@@ -724,24 +738,40 @@ __global__ void term_tables_kernel(const GridDesc g, const double* __restrict__ 
 
 // phi[s][z][:] = sum_i term_i[s][z][:] in FP64, rounded to FP32; term_i is
 // stored with the half-spectrum plane pitch (in floats).
+// Error-free sum of FP32 values (Knuth's TwoSum): s + e carries the running
+// sum with no rounding error beyond the compensation term, so the result is
+// the exact sum of the contributions up to its final rounding to FP32.  On
+// this GPU the FP64 pipe runs at a small fraction of the FP32 rate, and a
+// plain FP64 sum with its conversions costs an order of magnitude more.
+__device__ __forceinline__ void two_sum_acc(float& s, float& e, float x) {
+  const float t = s + x;
+  const float bb = t - s;
+  e += (s - (t - bb)) + (x - bb);
+  s = t;
+}
+
 __global__ void term_sum_kernel(const TermSumArgs a) {
-  const long long planes = (long long)a.m * a.nz;
-  const int vec_per_plane = a.plane_pts / 4;
-  const long long total = planes * vec_per_plane;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
-       q += (long long)gridDim.x * blockDim.x) {
-    const long long pl = q / vec_per_plane;
-    const int v = (int)(q - pl * vec_per_plane);
-    double4 acc = make_double4(0.0, 0.0, 0.0, 0.0);
-    for (int i = 0; i < a.k; ++i) {
-      const float4 x = __ldg(reinterpret_cast<const float4*>(a.term[i] + pl * a.plane_pitch) + v);
-      acc.x += (double)x.x;
-      acc.y += (double)x.y;
-      acc.z += (double)x.z;
-      acc.w += (double)x.w;
+  // blockIdx.y = plane (state, z); x-blocks stride over the plane's float4s
+  const long long pl = blockIdx.y;
+  const int nvec = a.plane_pts >> 2;
+  const float4* src[kMaxTermsK];
+#pragma unroll
+  for (int i = 0; i < kMaxTermsK; ++i)
+    src[i] = reinterpret_cast<const float4*>(a.term[i < a.k ? i : 0] + pl * a.plane_pitch);
+  float4* dst = reinterpret_cast<float4*>(a.phi_out + pl * a.plane_pts);
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += gridDim.x * blockDim.x) {
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < kMaxTermsK; ++i) {
+      if (i < a.k) {
+        const float4 x = __ldg(src[i] + v);
+        two_sum_acc(s[0], e[0], x.x);
+        two_sum_acc(s[1], e[1], x.y);
+        two_sum_acc(s[2], e[2], x.z);
+        two_sum_acc(s[3], e[3], x.w);
+      }
     }
-    reinterpret_cast<float4*>(a.phi_out + pl * a.plane_pts)[v] =
-        make_float4((float)acc.x, (float)acc.y, (float)acc.z, (float)acc.w);
+    dst[v] = make_float4(s[0] + e[0], s[1] + e[1], s[2] + e[2], s[3] + e[3]);
   }
 }
 
@@ -843,7 +873,9 @@ cudaError_t launch_plane(const GridDesc& g, const PlaneArgs<R>& a, cudaStream_t 
 cudaError_t launch_term_sum(const TermSumArgs& a, cudaStream_t st) {
   if (a.k < 1 || a.k > kMaxTermsK || (a.plane_pts & 3) || (a.plane_pitch & 3))
     return cudaErrorInvalidValue;
-  term_sum_kernel<<<8 * 152, 256, 0, st>>>(a);
+  const int nvec = a.plane_pts / 4;
+  dim3 grid((nvec + 255) / 256 < 8 ? (nvec + 255) / 256 : 8, (unsigned)((long long)a.m * a.nz));
+  term_sum_kernel<<<grid, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -34,6 +34,7 @@ struct Lane {
   R* f_full[kMaxTerms] = {}; // exp(-tau_i V)      (terms i >= 2)
   R* ktab = nullptr;         // per term: nxh + ny + nz propagation factors
   R* htab = nullptr;         // nxh + ny + nz kinetic values k^2/2
+  R* Vr = nullptr;           // [N] potential in precision R (internal layout)
   void* twx = nullptr;
   void* twy = nullptr;
   void* twz = nullptr;
@@ -213,6 +214,9 @@ int alloc_lane(itp_handle h, Lane<R>& L) {
   const size_t tl = (size_t)g.nxh + g.ny + g.nz;
   ITP_CUDA(h, cudaMalloc(&L.ktab, kMaxTerms * tl * sizeof(R)));
   ITP_CUDA(h, cudaMalloc(&L.htab, tl * sizeof(R)));
+  ITP_CUDA(h, cudaMalloc(&L.Vr, N * sizeof(R)));
+  if (h->have_V)
+    ITP_LAUNCH(h, ITP_KERNEL_OTHER, (launch_convert<double, R>(h->V, L.Vr, (long long)N, h->st)));
   std::vector<R> tx, ty, tz;
   roots_table<R>(g.nx, tx);
   roots_table<R>(g.ny, ty);
@@ -242,6 +246,7 @@ void free_lane(Lane<R>& L) {
   for (int i = 1; i < kMaxTerms; ++i) cudaFree(L.work_terms[i]);
   cudaFree(L.ktab);
   cudaFree(L.htab);
+  cudaFree(L.Vr);
   cudaFree(L.twx);
   cudaFree(L.twy);
   cudaFree(L.twz);
@@ -424,10 +429,15 @@ int energies_lane(itp_handle h, int flags) {
   ph.mode = PLANE_HPSI;
   ph.acc = h->acc;
   ph.V = h->V;
+  if (sizeof(R) == 4) {   // mixed: H psi in FP32 into psi_tmp
+    ph.V_r = L.Vr;
+    ph.phi_out = L.psi_tmp;
+  }
   ITP_LAUNCH(h, ITP_KERNEL_PLANE_HPSI, launch_plane<R>(g, ph, h->st));
   if (sizeof(R) == 4) {
-    ITP_LAUNCH(h, ITP_KERNEL_GRAM, (launch_tc_gram<float, double>(
-                                       reinterpret_cast<const float*>(L.psi), h->acc, h->m,
+    ITP_LAUNCH(h, ITP_KERNEL_GRAM, (launch_tc_gram<float, float>(
+                                       reinterpret_cast<const float*>(L.psi),
+                                       reinterpret_cast<const float*>(L.psi_tmp), h->m,
                                        g.n_points, h->n_chunks, h->partial, h->status, h->st)));
   } else {
     ITP_LAUNCH(h, ITP_KERNEL_GRAM, (launch_gram_partial<double, double, double>(
@@ -657,6 +667,12 @@ int itp_set_potential(itp_handle h, const double* V_host) {
                                       h->Vstage, h->V, h->g.nz, h->g.ny, h->g.nx, h->st)));
   h->f32.tab_order = 0;
   h->f64.tab_order = 0;
+  if (h->f32.ready)
+    ITP_LAUNCH(h, ITP_KERNEL_OTHER, (launch_convert<double, float>(h->V, h->f32.Vr,
+                                                                   h->g.n_points, h->st)));
+  if (h->f64.ready)
+    ITP_LAUNCH(h, ITP_KERNEL_OTHER, (launch_convert<double, double>(h->V, h->f64.Vr,
+                                                                    h->g.n_points, h->st)));
   h->have_V = true;
   return ITP_OK;
 }

@@ -47,6 +47,7 @@ struct PlaneArgs {
   double coef;               // c_i of the term
   int acc_init;              // 1: acc = c*u, 0: acc += c*u
   const double* V;           // [N] potential (PLANE_HPSI)
+  const R* V_r;              // [N] potential in R (PLANE_HPSI with phi_out: output in R)
   const void* twx;           // nx roots (complex R)
   const void* twy;           // ny roots
 };
@@ -63,9 +64,10 @@ struct PencilArgs {
   const void* twz;           // nz roots
 };
 
-// phi = sum_i term_i in FP64, rounded to FP32 (mixed path): term_i holds the
-// FP32 contribution c_i * f_i * u_i of term i, stored plane by plane with the
-// half-spectrum plane pitch (floats); phi is [m][N].
+// phi = sum_i term_i, exact up to the final rounding to FP32 (error-free
+// TwoSum accumulation; mixed path): term_i holds the FP32 contribution
+// c_i * f_i * u_i of term i, stored plane by plane with the half-spectrum
+// plane pitch (floats); phi is [m][N].
 constexpr int kMaxTermsK = 6;
 struct TermSumArgs {
   int m, k, nz, plane_pts;
