@@ -173,6 +173,33 @@ int itp_profile(itp_handle h, int enable);
  * the last itp_profile call.  Synchronises. */
 int itp_profile_read(itp_handle h, int kind, long long* launches, double* total_ms);
 
+/* Orthonormalise a block of states that already lives in device memory,
+ * without allocating any device memory: for callers that cannot call
+ * cudaMalloc -- code running inside a memory pool or arena that owns all
+ * device memory, a host process under a fixed device-memory budget, or a
+ * path that must not allocate between set-up and a deadline.  The paper has
+ * no counterpart; this computes the same FP64 orthonormalisation as
+ * itp_orthonormalize (S = Phi Phi^T dV = L L^T, psi = L^{-1} phi) on
+ * caller-owned buffers.
+ *   phi_device  [m][n_points] doubles on the current device (input, not
+ *               modified); any point order, the same for every state
+ *   psi_device  [m][n_points] doubles (output); must not overlap phi_device
+ *   m           1..128 states; n_points >= 1; dV > 0 the volume element
+ *   cuda_stream the stream to run on (NULL: default stream); the call
+ *               synchronises it before returning
+ * Returns ITP_OK, ITP_ERR_ARG (bad pointer or size, m > 128),
+ * ITP_ERR_NOT_PD (overlap not positive definite; psi_device then holds no
+ * meaningful values) or ITP_ERR_CUDA.
+ * Scratch space is a fixed array of about 4.3 MiB inside the library, present
+ * on every GPU that loads it until the process exits.  All calls on a device
+ * share it: calls whose work overlaps on the GPU (different streams or
+ * threads at the same time) race and must be serialised by the caller.  The
+ * first call on each device looks up the array's device address (with that
+ * device current); make that first call before capturing a stream into a
+ * CUDA graph. */
+int itp_orthonormalize_noalloc(const double* phi_device, double* psi_device, int m,
+                               long long n_points, double dV, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

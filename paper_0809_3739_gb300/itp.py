@@ -50,6 +50,8 @@ SIGNATURES = [
     ("itp_profile", _I, [_H, _I]),
     ("itp_profile_read", _I, [_H, _I, ctypes.POINTER(ctypes.c_longlong),
                               ctypes.POINTER(ctypes.c_double)]),
+    ("itp_orthonormalize_noalloc", _I, [ctypes.c_void_p, ctypes.c_void_p, _I, ctypes.c_longlong,
+                                        _D, ctypes.c_void_p]),
 ]
 
 KERNEL_KINDS = ["plane_fwd", "plane_merged", "plane_combine", "plane_hpsi", "pencil",
@@ -179,6 +181,18 @@ def itp_profile_read(h, kind: int):
     ms = ctypes.c_double(0.0)
     _check(h, load().itp_profile_read(h, int(kind), ctypes.byref(n), ctypes.byref(ms)))
     return int(n.value), float(ms.value)
+
+
+def itp_orthonormalize_noalloc(phi_device_ptr: int, psi_device_ptr: int, m: int,
+                               n_points: int, dV: float, cuda_stream: int = 0):
+    """Allocation-free orthonormalisation of caller-owned device buffers
+    (device pointers as integers, e.g. torch tensors' data_ptr())."""
+    code = load().itp_orthonormalize_noalloc(ctypes.c_void_p(phi_device_ptr),
+                                            ctypes.c_void_p(psi_device_ptr), int(m),
+                                            int(n_points), float(dV),
+                                            ctypes.c_void_p(cuda_stream or None))
+    if code != ITP_OK:
+        raise ItpError(code, "itp_orthonormalize_noalloc failed")
 
 
 # ---- a thin object wrapper -----------------------------------------------------
