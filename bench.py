@@ -182,6 +182,90 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def ho_closed_shells(n):
+    """E = n + 3/2 of the 3D oscillator, shell s with (s+1)(s+2)/2 states.
+    On the 128^3 / [-8,8)^3 grid the grid spectrum equals these values to
+    round-off for the first eight shells (120 states)."""
+    E = []
+    s = 0
+    while len(E) < n:
+        E += [s + 1.5] * ((s + 1) * (s + 2) // 2)
+        s += 1
+    return np.array(E[:n])
+
+
+def time_to_tol(P, precision, tol=1e-8, order=12, tau=0.5, n=120, guard=8,
+                max_fp32=400, max_fp64=200, plateau_rel=1e-5):
+    """Wall time from itp_set_states of seeded random states until every one
+    of the n lowest Ritz energies is within tol of its exact value (3D
+    harmonic oscillator, 128^3 grid, box [-8,8)^3, n = 120 = eight closed
+    shells).  FP64: FP64 steps throughout.  Mixed: FP32 steps while the
+    energies still change by more than plateau_rel * max|E| per step (the
+    FP32-evaluated energies level off near 1e-5 relative while the FP32
+    states keep converging), then as many further FP32 steps as the observed
+    convergence rate says the states need, then FP64 polish steps
+    (itp_polish, one step per call) until within tol.  The reference is used
+    only to stop the clock, never to steer the iteration."""
+    from itp_workloads import cubic, harmonic_potential, normal_states
+    g = cubic(128, 16.0)
+    V = harmonic_potential(g)
+    m = n + guard
+    psi = normal_states(m, g.n_points, seed=4321)
+    E_ref = ho_closed_shells(n)
+    h = P.ItpGrid(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, n, guard, precision)
+    h.set_potential(V)
+    h.synchronize()
+    t0 = time.perf_counter()
+    h.set_states(psi)
+    steps32 = steps64 = 0
+    err = float("inf")
+    E_prev = None
+    if precision == P.ITP_MIXED:
+        # FP32 steps until the FP32-evaluated energies stop moving; the
+        # states keep converging below that floor at the rate the energy
+        # changes showed before it, so a few more FP32 steps (as many as
+        # that rate needs to bring an energy change of the last clean step
+        # down to tol) precede the FP64 polish.
+        dEs = []
+        extra = None
+        while steps32 < max_fp32:
+            E = h.step(order, tau, ritz="values")
+            steps32 += 1
+            err = float(np.max(np.abs(E[:n] - E_ref)))
+            if err < tol:
+                break
+            if E_prev is not None:
+                dE = float(np.max(np.abs(E[:n] - E_prev[:n])))
+                if extra is not None:
+                    extra -= 1
+                    if extra <= 0:
+                        break
+                elif dE < plateau_rel * max(1.0, float(np.max(np.abs(E[:n])))):
+                    clean = [d for d in dEs[-4:] if d > 0]
+                    rates = [b / a for a, b in zip(clean, clean[1:]) if a > 0]
+                    rho = min(0.9, max(0.05, float(np.median(rates)))) if rates else 0.5
+                    extra = int(np.ceil(np.log(max(dEs[-1], tol) / tol) / np.log(1.0 / rho)))
+                    extra = min(extra, 60)
+                    if extra <= 0:
+                        break
+                dEs.append(dE)
+            E_prev = E
+        while err >= tol and steps64 < max_fp64:
+            _, E = h.polish(order, tau, 1e-300, 1)
+            steps64 += 1
+            err = float(np.max(np.abs(E[:n] - E_ref)))
+    else:
+        while err >= tol and steps64 < max_fp64:
+            E = h.step(order, tau, ritz="values")
+            steps64 += 1
+            err = float(np.max(np.abs(E[:n] - E_ref)))
+    h.synchronize()
+    dt = time.perf_counter() - t0
+    h.close()
+    return {"seconds": dt, "fp32_steps": steps32, "fp64_steps": steps64,
+            "max_abs_error_ha": err, "reached": err < tol}
+
+
 def time_steps(h, stream, order, tau, steps, torch):
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
@@ -204,6 +288,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path measurement")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance runs")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
@@ -344,6 +429,18 @@ def main():
                                   "share": round(v[1] / tot64, 4)} for k, v in prof64.items()}}
         h.close()
 
+    # ---- time to n states at tol: mixed vs FP64 --------------------------------
+    ttt = None
+    if not args.no_ttt:
+        barrier()
+        ttt = {"workload": "3D harmonic oscillator, 128^3 grid, box [-8,8)^3, n = 120 "
+                           "(eight closed shells, exact E = n + 3/2) + 8 guard, order 12, "
+                           "tau = 0.5, seeded random-normal start",
+               "tol_ha": 1e-8,
+               "mixed": time_to_tol(P, P.ITP_MIXED),
+               "fp64": time_to_tol(P, P.ITP_FP64)}
+        ttt["speedup_mixed_vs_fp64"] = ttt["fp64"]["seconds"] / ttt["mixed"]["seconds"]
+
     # ---- CPU oracle on a bounded sample (rank 0, N = 1 only) -------------------
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
@@ -378,6 +475,7 @@ def main():
             "roofline": roof,
             "kernel_breakdown": breakdown,
             "fp64_path": fp64,
+            "time_to_tol": ttt,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clk,

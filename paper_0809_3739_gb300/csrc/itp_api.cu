@@ -58,7 +58,8 @@ struct itp_grid {
   Lane<double> f64;
   bool cur64 = true;          // which lane holds the states
   bool have_V = false, have_states = false, have_phi = false;
-  int n_chunks = 0;
+  int n_chunks = 0;           // Gram partial sums (CUDA-core kernels)
+  int n_chunks_tc = 0;        // Gram partial sums (tensor-core kernel, one CTA per SM)
   double* partial = nullptr;  // [n_chunks][m][m]
   double* S = nullptr;        // [m][m]
   double* Mx = nullptr;       // [m][m]
@@ -388,11 +389,11 @@ int orthonormalize_lane<double>(itp_handle h) {
 template <>
 int orthonormalize_lane<float>(itp_handle h) {
   Lane<float>& L = h->f32;
-  ITP_LAUNCH(h, ITP_KERNEL_GRAM, (launch_tc_gram<float, float>(L.psi_tmp, L.psi_tmp, h->m,
-                                                               h->g.n_points, h->n_chunks,
+  ITP_LAUNCH(h, ITP_KERNEL_GRAM, (launch_tc_gram(L.psi_tmp, L.psi_tmp, h->m,
+                                                               h->g.n_points, h->n_chunks_tc,
                                                                h->partial, h->status, h->st)));
   ITP_LAUNCH(h, ITP_KERNEL_GRAM_REDUCE,
-             launch_gram_reduce(h->partial, h->n_chunks, h->m, h->dV, 1, h->S, h->st));
+             launch_gram_reduce(h->partial, h->n_chunks_tc, h->m, h->dV, 1, h->S, h->st));
   ITP_LAUNCH(h, ITP_KERNEL_CHOLESKY, launch_cholesky_inverse(h->S, h->m, h->Mx, h->status, h->st));
   ITP_LAUNCH(h, ITP_KERNEL_APPLY, (launch_tc_apply<float, float>(h->Mx, h->m, L.psi_tmp, L.psi,
                                                                  h->g.n_points, h->status,
@@ -435,16 +436,19 @@ int energies_lane(itp_handle h, int flags) {
   }
   ITP_LAUNCH(h, ITP_KERNEL_PLANE_HPSI, launch_plane<R>(g, ph, h->st));
   if (sizeof(R) == 4) {
-    ITP_LAUNCH(h, ITP_KERNEL_GRAM, (launch_tc_gram<float, float>(
+    ITP_LAUNCH(h, ITP_KERNEL_GRAM, (launch_tc_gram(
                                        reinterpret_cast<const float*>(L.psi),
                                        reinterpret_cast<const float*>(L.psi_tmp), h->m,
-                                       g.n_points, h->n_chunks, h->partial, h->status, h->st)));
+                                       g.n_points, h->n_chunks_tc, h->partial, h->status,
+                                       h->st)));
   } else {
     ITP_LAUNCH(h, ITP_KERNEL_GRAM, (launch_gram_partial<double, double, double>(
                                        reinterpret_cast<const double*>(L.psi), h->acc, h->m,
                                        g.n_points, h->n_chunks, h->partial, h->st)));
   }
-  ITP_LAUNCH(h, ITP_KERNEL_GRAM_REDUCE, launch_gram_reduce(h->partial, h->n_chunks, h->m, h->dV, 1, h->Hs, h->st));
+  const int chunks = sizeof(R) == 4 ? h->n_chunks_tc : h->n_chunks;
+  ITP_LAUNCH(h, ITP_KERNEL_GRAM_REDUCE,
+             launch_gram_reduce(h->partial, chunks, h->m, h->dV, 1, h->Hs, h->st));
   if (flags & ITP_RITZ) {
     ITP_LAUNCH(h, ITP_KERNEL_EIGH, launch_jacobi_eigh(h->Hs, h->m, h->E_dev, h->Mx, h->Wmm, h->status, h->st));
     if (sizeof(R) == 4) {
@@ -593,6 +597,7 @@ int itp_create_grid(itp_handle* out, int nx, int ny, int nz, double lx, double l
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
   h->n_chunks = 2 * sms;
+  h->n_chunks_tc = sms;
   const size_t N = (size_t)g.n_points, m = (size_t)h->m;
   int rc;
 #define ITP_CREATE(expr)           \

@@ -138,9 +138,10 @@ cudaError_t launch_apply_matrix(const double* M, int m, int lower, const TX* X, 
                                 long long n_points, cudaStream_t st);
 // Tensor-core (tcgen05 TF32, 3xTF32 split) versions, m <= 128; status gets
 // bit 4 if a bounded mbarrier wait expired.
-template <typename TA, typename TB>
-cudaError_t launch_tc_gram(const TA* A, const TB* B, int m, long long n_points, int n_chunks,
-                           double* partial, int* status, cudaStream_t st);
+// Gram: FP32 operands (16-byte aligned, n_points % 8 == 0) streamed in by
+// bulk copies; A == B computes A A^T with one operand tile per step.
+cudaError_t launch_tc_gram(const float* A, const float* B, int m, long long n_points,
+                           int n_chunks, double* partial, int* status, cudaStream_t st);
 template <typename TX, typename TY>
 cudaError_t launch_tc_apply(const double* M, int m, const TX* X, TY* Y, long long n_points,
                             int* status, cudaStream_t st);

@@ -19,8 +19,12 @@
 //
 // Every wait on an mbarrier is bounded; on expiry the kernel records
 // ITP status bit 4 and carries on, so no launch can hang.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <stdint.h>
+
+#include <mutex>
 
 #include "itp_kernels.cuh"
 
@@ -158,6 +162,23 @@ __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) 
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
 }
 
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// 2D tensor-map (TMA) load of one box into shared memory, completing on the
+// mbarrier's transaction count.  x is the innermost (point) coordinate.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
                                              uint32_t d) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
@@ -167,16 +188,12 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
 
 template <typename T> __device__ __forceinline__ float ldf(const T* p) { return (float)__ldg(p); }
 
-// Four consecutive values as floats (16-byte aligned for float, 32 for double).
+// Four consecutive floats (16-byte aligned).
 __device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
   const float4 q = __ldg(reinterpret_cast<const float4*>(p));
   v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
 }
-__device__ __forceinline__ void ld4(const double* p, float (&v)[4]) {
-  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
-  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
-  v[0] = (float)a.x; v[1] = (float)a.y; v[2] = (float)b.x; v[3] = (float)b.y;
-}
+
 
 // ---------------------------------------------------------------------------
 // Gram partial sums.  Tile = 128 rows x 32 points; two pipeline stages.
@@ -184,58 +201,41 @@ constexpr int kGramKT = 32;                          // points per tile
 constexpr int kGramKC = kGramKT / 4;                 // 4-element K chunks
 constexpr int kTileBytes = 128 * kGramKT * 4;        // 16 KB per operand part
 
-// Stage one operand tile of rows [0,128) x points [p0, p0+32) as hi/lo TF32.
-template <typename T>
-__device__ __forceinline__ void stage_rows(const T* __restrict__ X, int m, long long N,
-                                           long long p0, long long p_end, uint32_t hi_base,
-                                           uint32_t lo_base) {
-  // 1024 groups of (row, 4 points); lanes 0..7 of a group of 8 take rows
-  // r%8 = 0..7 so the 16-byte shared stores are conflict-free.
-#pragma unroll
-  for (int q = 0; q < 1024 / kTcThreads; ++q) {
-    const int L = threadIdx.x + kTcThreads * q;
-    const int r = (L >> 6) * 8 + (L & 7);
-    const int k4 = (L >> 3) & 7;
-    const long long p = p0 + 4 * k4;
-    float v[4] = {0.f, 0.f, 0.f, 0.f};
-    if (r < m) {
-      const T* src = X + (long long)r * N + p;
-      if (p + 3 < p_end) {
-        ld4(src, v);
-      } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          if (p + e < p_end) v[e] = ldf(src + e);
-      }
-    }
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) split_tf32(v[e], h[e], l[e]);
-    const uint32_t off = (uint32_t)(((r >> 3) * kGramKC + k4) * 128 + (r & 7) * 16);
-    st_shared_v4(hi_base + off, h[0], h[1], h[2], h[3]);
-    st_shared_v4(lo_base + off, l[0], l[1], l[2], l[3]);
-  }
-}
+// Raw tiles (128 state rows x 32 points, FP32) arrive by one 2D TMA load
+// per operand into a ring of RAW stages, 128-byte swizzled: 16-byte chunk c
+// of row r sits at chunk position c ^ (r % 8), so the converters' column
+// reads are free of bank conflicts.  Rows beyond m and points beyond N are
+// zero-filled by the TMA.  All warps convert a raw tile into the hi/lo
+// canonical layout of one of two MMA stages; one thread issues the MMAs.
+constexpr int kRawBytes = 128 * kGramKT * 4;        // 16 KB per operand
 
-template <typename TA, typename TB>
+template <bool SAME>
 __global__ void __launch_bounds__(kTcThreads, 1)
-    tc_gram_kernel(const TA* __restrict__ A, const TB* __restrict__ B, int m, long long N,
-                   long long chunk, double* __restrict__ partial, int* status) {
+    tc_gram_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   int m, long long N, long long chunk, double* __restrict__ partial,
+                   int* status) {
+  constexpr int NOPS = SAME ? 1 : 2;                // operands per tile
+  constexpr int RAW = SAME ? 4 : 3;                 // raw ring depth
   extern __shared__ __align__(1024) unsigned char smraw[];
-  const bool same = (const void*)A == (const void*)B;
-  // stage s: A_hi, A_lo, B_hi, B_lo (B parts unused when A == B)
-  unsigned char* base = smraw;
-  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(8) uint64_t full[RAW];
+  __shared__ __align__(8) uint64_t mma_done[2];
   __shared__ uint32_t tmem_base;
-  const uint32_t sbase = smem_u32(base);
-  auto part = [&](int s, int which) { return sbase + (uint32_t)((s * 4 + which) * kTileBytes); };
+  const uint32_t sbase = (smem_u32(smraw) + 1023u) & ~1023u;   // 1 KB for the swizzle
+  unsigned char* sgen = smraw + (sbase - smem_u32(smraw));
+  auto canon = [&](int c, int op, int part) {   // part 0 = hi, 1 = lo
+    return sbase + (uint32_t)(((c * NOPS + op) * 2 + part) * kTileBytes);
+  };
+  const uint32_t raw_off = (uint32_t)(2 * NOPS * 2 * kTileBytes);
+  auto raw = [&](int r, int op) { return sbase + raw_off + (uint32_t)((r * NOPS + op) * kRawBytes); };
 
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int r = 0; r < RAW; ++r) mbar_init(&full[r], 1);
+    mbar_init(&mma_done[0], 1);
+    mbar_init(&mma_done[1], 1);
     fence_barrier_init();
   }
-  if (threadIdx.x < 32) tmem_alloc(&tmem_base, 128);
+  if (warp == 0) tmem_alloc(&tmem_base, 128);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -244,21 +244,49 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const long long p_begin = (long long)blockIdx.x * chunk;
   const long long p_end = min(N, p_begin + chunk);
   const int ntiles = p_end > p_begin ? (int)((p_end - p_begin + kGramKT - 1) / kGramKT) : 0;
+
+  auto issue = [&](int t, int r) {   // one thread
+    const int x = (int)(p_begin + (long long)t * kGramKT);
+    mbar_arrive_expect_tx(&full[r], (uint32_t)(NOPS * kRawBytes));
+    tma_load_2d(raw(r, 0), &tmA, x, 0, &full[r]);
+    if (!SAME) tma_load_2d(raw(r, 1), &tmB, x, 0, &full[r]);
+  };
+  if (threadIdx.x == 0)
+    for (int t = 0; t < RAW && t < ntiles; ++t) issue(t, t);
+
   constexpr uint32_t idesc = idesc_tf32(128, 128);
   const uint32_t sbo = kGramKC * 128;
-
   for (int t = 0; t < ntiles; ++t) {
-    const int s = t & 1;
-    if (t >= 2) mbar_wait(&bar[s], (uint32_t)(((t - 2) >> 1) & 1), status);
-    const long long p0 = p_begin + (long long)t * kGramKT;
-    stage_rows(A, m, N, p0, p_end, part(s, 0), part(s, 1));
-    if (!same) stage_rows(B, m, N, p0, p_end, part(s, 2), part(s, 3));
+    const int r = t % RAW, c = t & 1;
+    mbar_wait(&full[r], (uint32_t)((t / RAW) & 1), status);
+    if (t >= 2) mbar_wait(&mma_done[c], (uint32_t)(((t - 2) >> 1) & 1), status);
+#pragma unroll
+    for (int op = 0; op < NOPS; ++op) {
+      const unsigned char* rp = sgen + raw_off + (r * NOPS + op) * kRawBytes;
+#pragma unroll
+      for (int q = 0; q < 1024 / kTcThreads; ++q) {
+        const int L = threadIdx.x + kTcThreads * q;
+        const int row = (L >> 6) * 8 + (L & 7);
+        const int k4 = (L >> 3) & 7;
+        const float4 x =
+            *reinterpret_cast<const float4*>(rp + row * 128 + ((k4 ^ (row & 7)) << 4));
+        uint32_t h[4], l[4];
+        split_tf32(x.x, h[0], l[0]);
+        split_tf32(x.y, h[1], l[1]);
+        split_tf32(x.z, h[2], l[2]);
+        split_tf32(x.w, h[3], l[3]);
+        const uint32_t off = (uint32_t)(((row >> 3) * kGramKC + k4) * 128 + (row & 7) * 16);
+        st_shared_v4(canon(c, op, 0) + off, h[0], h[1], h[2], h[3]);
+        st_shared_v4(canon(c, op, 1) + off, l[0], l[1], l[2], l[3]);
+      }
+    }
     fence_async_smem();
+    tc_fence_before();
     __syncthreads();
     if (threadIdx.x == 0) {
       tc_fence_after();
-      const uint32_t ahi = part(s, 0), alo = part(s, 1);
-      const uint32_t bhi = same ? ahi : part(s, 2), blo = same ? alo : part(s, 3);
+      const uint32_t ahi = canon(c, 0, 0), alo = canon(c, 0, 1);
+      const uint32_t bhi = canon(c, NOPS - 1, 0), blo = canon(c, NOPS - 1, 1);
 #pragma unroll
       for (int ks = 0; ks < kGramKT / 8; ++ks) {
         const uint32_t koff = ks * 256;   // 8 TF32 = two core matrices along K
@@ -270,28 +298,29 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         mma_tf32(tmem, dah, dbl, idesc, 1u);
         mma_tf32(tmem, dal, dbh, idesc, 1u);
       }
-      mma_commit(&bar[s]);
+      mma_commit(&mma_done[c]);
+      // raw slot r was consumed by every thread before the barrier above
+      if (t + RAW < ntiles) issue(t + RAW, r);
     }
   }
   double* out = partial + (long long)blockIdx.x * m * m;
   if (ntiles > 0) {
     const int tl = ntiles - 1;
-    mbar_wait(&bar[tl & 1], (uint32_t)((tl >> 1) & 1), status);
+    mbar_wait(&mma_done[tl & 1], (uint32_t)((tl >> 1) & 1), status);
     tc_fence_after();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // warp w reads TMEM lane quadrant w % 4; warps 4.. take the upper column halves
     const int quad = warp & 3, chalf = warp >> 2;
     const int i = quad * 32 + lane;
 #pragma unroll
     for (int cc = 0; cc < 2; ++cc) {
-      const int c = chalf * 2 + cc;
-      uint32_t r[32];
-      tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * 32), r);
+      const int cb = chalf * 2 + cc;
+      uint32_t rr[32];
+      tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cb * 32), rr);
       if (i < m) {
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
-          const int j = c * 32 + q;
-          if (j < m) out[(long long)i * m + j] = (double)__uint_as_float(r[q]);
+          const int j = cb * 32 + q;
+          if (j < m) out[(long long)i * m + j] = (double)__uint_as_float(rr[q]);
         }
       }
     }
@@ -300,10 +329,39 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (threadIdx.x < 32) {
+  if (warp == 0) {
     tc_fence_after();
     tmem_dealloc(tmem, 128);
   }
+}
+
+// Driver entry point for tensor-map encoding (no link-time libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// Tensor map of an m x N row-major FP32 block, box 32 points x 128 rows,
+// 128-byte swizzle, out-of-range elements read as zero.
+bool make_rows_map(CUtensorMap* tm, const float* X, int m, long long N) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)m};
+  cuuint64_t strides[1] = {(cuuint64_t)N * sizeof(float)};
+  cuuint32_t box[2] = {(cuuint32_t)kGramKT, 128u};
+  cuuint32_t estr[2] = {1u, 1u};
+  return fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(X), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // ---------------------------------------------------------------------------
@@ -486,18 +544,33 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 }  // namespace
 
-template <typename TA, typename TB>
-cudaError_t launch_tc_gram(const TA* A, const TB* B, int m, long long n_points, int n_chunks,
-                           double* partial, int* status, cudaStream_t st) {
-  if (m > 128 || m < 1) return cudaErrorInvalidValue;
+cudaError_t launch_tc_gram(const float* A, const float* B, int m, long long n_points,
+                           int n_chunks, double* partial, int* status, cudaStream_t st) {
+  if (m > 128 || m < 1 || (n_points % 8) || n_points >= (1LL << 31)) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15)
+    return cudaErrorInvalidValue;
   long long chunk = (n_points + n_chunks - 1) / n_chunks;
   chunk = (chunk + kGramKT - 1) / kGramKT * kGramKT;
-  const size_t smem = 2 * 4 * (size_t)kTileBytes;   // 128 KB
-  cudaError_t e = cudaFuncSetAttribute(tc_gram_kernel<TA, TB>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  tc_gram_kernel<TA, TB><<<n_chunks, kTcThreads, smem, st>>>(A, B, m, n_points, chunk, partial,
-                                                             status);
+  const bool same = A == B;
+  CUtensorMap tmA, tmB;
+  if (!make_rows_map(&tmA, A, m, n_points) || !make_rows_map(&tmB, B, m, n_points))
+    return cudaErrorNotSupported;
+  const int nops = same ? 1 : 2, raw = same ? 4 : 3;
+  const size_t smem = (size_t)2 * nops * 2 * kTileBytes + (size_t)raw * nops * kRawBytes + 1024;
+  cudaError_t e;
+  if (same) {
+    e = cudaFuncSetAttribute(tc_gram_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    tc_gram_kernel<true><<<n_chunks, kTcThreads, smem, st>>>(tmA, tmB, m, n_points, chunk,
+                                                             partial, status);
+  } else {
+    e = cudaFuncSetAttribute(tc_gram_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    tc_gram_kernel<false><<<n_chunks, kTcThreads, smem, st>>>(tmA, tmB, m, n_points, chunk,
+                                                              partial, status);
+  }
   return cudaGetLastError();
 }
 
@@ -519,10 +592,6 @@ cudaError_t launch_tc_apply(const double* M, int m, const TX* X, TY* Y, long lon
   return cudaGetLastError();
 }
 
-template cudaError_t launch_tc_gram<float, float>(const float*, const float*, int, long long, int,
-                                                  double*, int*, cudaStream_t);
-template cudaError_t launch_tc_gram<float, double>(const float*, const double*, int, long long,
-                                                   int, double*, int*, cudaStream_t);
 template cudaError_t launch_tc_apply<float, float>(const double*, int, const float*, float*,
                                                    long long, int*, cudaStream_t);
 

@@ -252,3 +252,16 @@ def test_ritz_rotation_preserves_trace_and_span():
     # the rotated states diagonalise the subspace matrix
     Hs = Psi1 @ HPsi1.T * g.dV
     assert np.max(np.abs(Hs - np.diag(E1))) < 1e-12 * np.max(np.abs(E1))
+
+
+def test_ho_grid_spectrum_128_closed_shells():
+    """The time-to-tolerance workload: 128^3 grid, box [-8,8)^3, V = r^2/2.
+    Its 120 lowest grid eigenvalues are the first eight closed shells
+    E = n + 3/2 (degeneracies 1, 3, ..., 36) to round-off, so n + 3/2 is
+    an exact reference for them."""
+    g = cubic(128, 16.0)
+    E = D.ho_grid_spectrum(g, 121)
+    want = np.concatenate([[nn + 1.5] * ((nn + 1) * (nn + 2) // 2) for nn in range(8)])
+    assert len(want) == 120
+    assert np.max(np.abs(E[:120] - want)) < 1e-11
+    assert abs(E[120] - 9.5) < 1e-11
