@@ -44,6 +44,12 @@ WORKLOADS = {
                     desc="C60-like Gaussian well (60 wells, depth 2.0 Ha, sigma 0.8 bohr, "
                          "radius 6.7 bohr), 128^3 grid, box 32 bohr, n=120 + 8 guard states, "
                          "order 12 (k_i = 1..6), tau = 0.25"),
+    # the same grid and potential with 16 states: a case small enough for
+    # full ncu captures (the half spectrum, 136 MB, still exceeds L2)
+    "c60_128_m16": dict(n=128, box=32.0, potential="c60", n_states=16, n_guard=0, order=12,
+                        tau=0.25, seed=1234,
+                        desc="C60-like Gaussian well, 128^3 grid, box 32 bohr, 16 states, "
+                             "order 12, tau = 0.25 (profiling case)"),
     "ho_32": dict(n=32, box=16.0, potential="ho", n_states=10, n_guard=2, order=4, tau=0.1,
                   seed=1234, desc="3D harmonic oscillator, 32^3 grid, box [-8,8)^3, n=10 + 2 "
                                   "guard, order 4, tau = 0.1"),
@@ -62,6 +68,31 @@ def make_inputs(w, rank=0):
     m = w["n_states"] + w["n_guard"]
     psi = normal_states(m, g.n_points, seed=w["seed"], problem=rank)
     return g, V, psi
+
+
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum)
+# from ncu captures summarised in profiles/, scaled to the full launch by the
+# number of states, with the SHA-1 of the kernel source the counters were
+# taken on: a kernel changed since then reports no traffic.
+NCU_TRAFFIC = {
+    ("c60_128", "pencil"): {"bytes": 1.7155e9, "source": "paper_0809_3739_gb300/csrc/fft_passes.cu",
+                            "sha1": "bae3f771f195db06c8e0c76f0ceb75d4c4fc941e",
+                            "profile": "profiles/pencil_c60_128.md"},
+}
+
+
+def ncu_traffic(workload, kind):
+    import hashlib
+    rec = NCU_TRAFFIC.get((workload, kind))
+    if rec is None:
+        return None
+    try:
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() != rec["sha1"]:
+                return None
+    except OSError:
+        return None
+    return rec["bytes"]
 
 
 def algorithmic_bytes(kind, g, m, s):
@@ -372,7 +403,7 @@ def main():
         achieved = ab / per_launch_s / 1e9
         roof = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
                 "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": None, "algorithmic_bytes_per_launch": ab,
+                "traffic": ncu_traffic(args.workload, top), "algorithmic_bytes_per_launch": ab,
                 "avg_launch_ms": per_launch_s * 1e3}
     total_prof = sum(v[1] for v in kinds.values())
     breakdown = {k: {"launches": v[0], "ms": round(v[1], 3),

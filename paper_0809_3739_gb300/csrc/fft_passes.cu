@@ -340,6 +340,126 @@ __device__ __forceinline__ void x_merge(const PlaneGeo<R, NX, NY>& G, typename C
   }
 }
 
+// ---- stage B of the x transform fused with the real-FFT split / merge --------
+// One row pair per group of r2 lanes (32 / r2 rows per warp): lane b owns the
+// frequencies k = b + r2*k1 (k1 < r1) of its row, which are exactly the
+// outputs of its forward stage-B task; the partner frequencies nx - k sit in
+// lane (r2 - b) % r2 of the same group and arrive by warp shuffles.
+template <int R1, typename R, int NX, int NY, typename C>
+__device__ __forceinline__ void xB_fwd_split_r(const PlaneGeo<R, NX, NY>& G, C* sm) {
+  constexpr int NW = PlaneGeo<R, NX, NY>::NT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp >= NW) return;
+  const int r2 = G.ax.r2, rpw = 32 / r2;
+  const int grp = lane / r2, b = lane - grp * r2;
+  const int ngroups = (G.npair + rpw - 1) / rpw;
+  const int src = grp * r2 + (r2 - b) % r2;
+  const int half = G.nx >> 1;
+  for (int rg = warp; rg < ngroups; rg += NW) {
+    const int t = rg * rpw + grp;
+    const bool active = grp < rpw && t < G.npair;
+    C* row = sm + (active ? t : 0) * G.pp;
+    C a[R1];
+#pragma unroll
+    for (int i = 0; i < R1; ++i) a[i] = active ? row[swz(i + R1 * b)] : C{0, 0};
+    Dft<R1, -1, C>::run(a);   // a[k1] = Z[b + r2*k1]
+    C zm[R1];
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      // the receiver wants Z[nx - k]; its sender (lane src) holds it at index
+      // (R1 - k1) % R1 when b == 0 and R1 - 1 - k1 otherwise
+      const C mine = (b == 0) ? a[(R1 - k1) % R1] : a[R1 - 1 - k1];
+      zm[k1].x = __shfl_sync(0xffffffffu, mine.x, src);
+      zm[k1].y = __shfl_sync(0xffffffffu, mine.y, src);
+    }
+    __syncwarp();
+    if (active) {
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) {
+        const int k = b + r2 * k1;
+        if (k <= half) {
+          C A, B;
+          A.x = (R)0.5 * (a[k1].x + zm[k1].x);
+          A.y = (R)0.5 * (a[k1].y - zm[k1].y);
+          B.x = (R)0.5 * (a[k1].y + zm[k1].y);
+          B.y = (R)0.5 * (zm[k1].x - a[k1].x);
+          row[k] = A;
+          row[G.nxh + k] = B;
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Inverse: each lane builds its stage-B' inputs Z[b + r2*a] (a < r1) from
+// the half-spectrum rows A, B (Hermitian extension, imaginary parts of the
+// self-conjugate bins dropped), the row's lanes synchronise, then stage B'.
+template <int R1, typename R, int NX, int NY, typename C>
+__device__ __forceinline__ void xB_inv_merge_r(const PlaneGeo<R, NX, NY>& G, C* sm, const C* tw) {
+  constexpr int NW = PlaneGeo<R, NX, NY>::NT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp >= NW) return;
+  const int r2 = G.ax.r2, rpw = 32 / r2;
+  const int grp = lane / r2, b = lane - grp * r2;
+  const int ngroups = (G.npair + rpw - 1) / rpw;
+  const int half = G.nx >> 1;
+  for (int rg = warp; rg < ngroups; rg += NW) {
+    const int t = rg * rpw + grp;
+    const bool active = grp < rpw && t < G.npair;
+    C* row = sm + (active ? t : 0) * G.pp;
+    C v[R1];
+#pragma unroll
+    for (int i = 0; i < R1; ++i) {
+      const int k = b + r2 * i;
+      C z = C{0, 0};
+      if (active) {
+        if (k <= half) {
+          C A = row[k], B = row[G.nxh + k];
+          if (k == 0 || k == half) { A.y = 0; B.y = 0; }
+          z.x = A.x - B.y;
+          z.y = A.y + B.x;
+        } else {
+          const C A = row[G.nx - k], B = row[G.nxh + G.nx - k];
+          z.x = A.x + B.y;
+          z.y = B.x - A.y;
+        }
+      }
+      v[i] = z;
+    }
+    __syncwarp();
+    Dft<R1, 1, C>::run(v);
+    if (R1 > 1) {
+#pragma unroll
+      for (int i = 1; i < R1; ++i) v[i] = cmulc(v[i], tw[i * b]);
+    }
+    if (active) {
+#pragma unroll
+      for (int i = 0; i < R1; ++i) row[swz(i + R1 * b)] = v[i];
+    }
+    __syncwarp();
+  }
+}
+
+template <typename R, int NX, int NY, typename C>
+__device__ __forceinline__ void xB_fwd_split(const PlaneGeo<R, NX, NY>& G, C* sm, const C* tw) {
+  if (G.ax.r1 == 1 || G.ax.r2 > 32) {   // single-stage rows: split on its own
+    x_split(G, sm);
+    return;
+  }
+  ITP_WITH_RADIX(G.ax.r1, xB_fwd_split_r, G, sm)
+}
+template <typename R, int NX, int NY, typename C>
+__device__ __forceinline__ void xB_inv_merge(const PlaneGeo<R, NX, NY>& G, C* sm, const C* tw) {
+  if (G.ax.r1 == 1 || G.ax.r2 > 32) {
+    x_merge(G, sm);
+    __syncthreads();
+    xB<1>(G, sm, tw);
+    return;
+  }
+  ITP_WITH_RADIX(G.ax.r1, xB_inv_merge_r, G, sm, tw)
+}
+
 // ---- y stages (columns) -------------------------------------------------------
 // Inverse stage B' with the global load fused in: column t, block b reads
 // the frequencies ky = b + r2*a (a < r1) straight from the half spectrum.
@@ -556,9 +676,7 @@ __global__ void __launch_bounds__(launch_threads(PlaneGeo<R, NX, NY>::NT),
     __syncthreads();
     yA<1>(G, sm, twy);
     __syncthreads();
-    x_merge(G, sm);
-    __syncthreads();
-    xB<1>(G, sm, twx);
+    xB_inv_merge(G, sm, twx);
     __syncthreads();
     if constexpr (MODE == PLANE_MERGED) {
       EpiMerged<R> epi{reinterpret_cast<const C*>(a.f_mid + fac_off), G.npair, G.ax.r1};
@@ -587,10 +705,8 @@ __global__ void __launch_bounds__(launch_threads(PlaneGeo<R, NX, NY>::NT),
       return;
     }
   }
-  // forward x (stage B), split, forward y
-  xB<-1>(G, sm, twx);
-  __syncthreads();
-  x_split(G, sm);
+  // forward x (stage B fused with the split), forward y
+  xB_fwd_split(G, sm, twx);
   __syncthreads();
   yA<-1>(G, sm, twy);
   __syncthreads();
