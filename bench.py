@@ -406,6 +406,19 @@ def main():
                 "traffic": ncu_traffic(args.workload, top), "algorithmic_bytes_per_launch": ab,
                 "avg_launch_ms": per_launch_s * 1e3}
     total_prof = sum(v[1] for v in kinds.values())
+    # the same steps replayed from a CUDA graph (itp_step): one launch per step
+    h.step_graph(order, tau)   # capture
+    barrier()
+    gstart = torch.cuda.Event(enable_timing=True)
+    gend = torch.cuda.Event(enable_timing=True)
+    gstart.record(stream)
+    for _ in range(args.steps):
+        h.step_graph(order, tau)
+    gend.record(stream)
+    gend.synchronize()
+    dt_graph = gstart.elapsed_time(gend) / 1e3
+    graph = {"value": world * m * args.steps / dt_graph, "unit": "state-steps/s",
+             "ms_per_step": 1e3 * dt_graph / args.steps, "steps": args.steps}
     breakdown = {k: {"launches": v[0], "ms": round(v[1], 3),
                      "share": round(v[1] / total_prof, 4)} for k, v in kinds.items()}
     h.close()
@@ -505,6 +518,7 @@ def main():
             "gpu_launches": launches,
             "roofline": roof,
             "kernel_breakdown": breakdown,
+            "graph_replay": graph,
             "fp64_path": fp64,
             "time_to_tol": ttt,
             "e2e": e2e,

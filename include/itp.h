@@ -26,7 +26,7 @@
  *  - Ownership: the library owns all device memory of a handle.  Host arrays
  *    passed in are copied during the call and may be reused on return.
  *  - Streams: all device work of a handle is issued on the CUDA stream given
- *    at creation (NULL = legacy default stream), in call order.  Calls that
+ *    at creation (or on a stream the handle creates), in call order.  Calls that
  *    return host data (itp_energies, itp_get_states, itp_polish,
  *    itp_synchronize) synchronise that stream; the others do not.
  *  - Errors: every int-returning call returns ITP_OK (0) or an ITP_ERR_*
@@ -128,6 +128,16 @@ int itp_orthonormalize(itp_handle h);
  *   E_host may be NULL.  Synchronises; returns a pending ITP_ERR_NOT_PD /
  *   ITP_ERR_NOCONV. */
 int itp_energies(itp_handle h, double* E_host, int flags);
+
+/* One whole step -- itp_propagate(order, tau), itp_orthonormalize,
+ * itp_energies(flags) -- replayed from a CUDA graph.  The first call for a
+ * given (order, tau, flags, precision lane) captures the step's kernels and
+ * the copy of the energies into a graph on the handle's stream; later calls
+ * launch the graph (one launch instead of ~60).  flags: 0 or
+ * ITP_RITZ_VALUES (ITP_RITZ moves the states between buffers and is not
+ * captured).  Synchronises; E_host (nullable) receives the m energies.
+ * Per-kernel profiling (itp_profile) does not see graph replays. */
+int itp_step(itp_handle h, int order, double tau, int flags, double* E_host);
 
 /* Mixed precision only: switch the states to FP64 and iterate FP64 steps
  * (propagate, orthonormalise, Ritz values) until

@@ -4,5 +4,5 @@ ctypes binding."""
 from .itp import (ITP_FP64, ITP_MIXED, ITP_RITZ, ITP_RITZ_VALUES, ItpError, ItpGrid,  # noqa: F401
                   itp_create_grid, itp_destroy, itp_orthonormalize_noalloc, itp_energies, itp_get_phi, itp_get_states,
                   itp_kernel_launches, itp_last_error, itp_orthonormalize, itp_polish,
-                  itp_propagate, itp_set_potential, itp_set_states, itp_set_states_device,
+                  itp_propagate, itp_set_potential, itp_set_states, itp_set_states_device, itp_step,
                   itp_synchronize, itp_profile, itp_profile_read, load)

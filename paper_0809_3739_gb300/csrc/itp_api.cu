@@ -71,6 +71,13 @@ struct itp_grid {
   double* E_host_pinned = nullptr;
   long long launches = 0;
   std::string err;
+  bool own_stream = false;    // created by the library (no stream given)
+  // CUDA graph of one step (itp_step): propagate + orthonormalize + energies
+  cudaGraphExec_t step_exec = nullptr;
+  int step_order = 0, step_flags = -1, step_lane = -1;
+  double step_tau = 0.0;
+  bool capturing = false;
+  long long step_launches = 0;
   // optional per-kernel event timing (itp_profile)
   bool prof = false;
   struct ProfEvent { int kind; cudaEvent_t start, stop; };
@@ -115,7 +122,7 @@ int fail(itp_handle h, int code, const char* fmt, ...) {
   } while (0)
 
 long prof_begin(itp_handle h, int kind) {
-  if (!h->prof) return -1;
+  if (!h->prof || h->capturing) return -1;
   if (h->prof_used == h->prof_events.size()) {
     itp_grid::ProfEvent e{kind, nullptr, nullptr};
     if (cudaEventCreate(&e.start) != cudaSuccess || cudaEventCreate(&e.stop) != cudaSuccess)
@@ -531,6 +538,39 @@ int do_energies(itp_handle h, double* E_host, int flags) {
   return ITP_OK;
 }
 
+// Device work of one step, stream-ordered, no host synchronisation.
+template <typename R>
+int step_work(itp_handle h, int k, double tau, int flags) {
+  ITP_TRY(propagate_lane<R>(h, k, tau));
+  ITP_TRY(orthonormalize_lane<R>(h));
+  ITP_TRY(energies_lane<R>(h, flags));
+  ITP_CUDA(h, cudaMemcpyAsync(h->E_host_pinned, h->E_dev, h->m * sizeof(double),
+                              cudaMemcpyDeviceToHost, h->st));
+  ITP_CUDA(h, cudaMemcpyAsync(h->status_host, h->status, sizeof(int), cudaMemcpyDeviceToHost,
+                              h->st));
+  return ITP_OK;
+}
+
+// Everything a step allocates or builds once, done outside any capture.
+template <typename R>
+int step_resources(itp_handle h, int k, double tau) {
+  Lane<R>& L = lane_of<R>(h);
+  ITP_TRY(prepare_tables<R>(h, L, k, tau));
+  if (sizeof(R) == 4 && L.fused_ok) {
+    L.work_terms[0] = L.work;
+    for (int i = 1; i < k; ++i) {
+      if (!L.work_terms[i] &&
+          cudaMalloc(&L.work_terms[i], (size_t)h->m * h->g.n_half * 2 * sizeof(R)) !=
+              cudaSuccess) {
+        cudaGetLastError();
+        L.fused_ok = false;
+        break;
+      }
+    }
+  }
+  return ITP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -592,6 +632,12 @@ int itp_create_grid(itp_handle* out, int nx, int ny, int nz, double lx, double l
   h->m = n_states + n_guard;
   h->precision = precision;
   h->st = (cudaStream_t)cuda_stream;
+  if (!h->st) {
+    // a stream of its own, so that steps can be captured into a CUDA graph
+    if (cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking) != cudaSuccess)
+      return bail(fail(h, ITP_ERR_CUDA, "cannot create a stream"));
+    h->own_stream = true;
+  }
   if (cudaGetDevice(&h->device) != cudaSuccess)
     return bail(fail(h, ITP_ERR_CUDA, "no CUDA device"));
   int sms = 152;
@@ -642,6 +688,7 @@ void itp_destroy(itp_handle h) {
   cudaSetDevice(h->device);
   if (h->st) cudaStreamSynchronize(h->st);
   else cudaDeviceSynchronize();
+  if (h->step_exec) cudaGraphExecDestroy(h->step_exec);
   free_lane(h->f32);
   free_lane(h->f64);
   cudaFree(h->V);
@@ -660,6 +707,7 @@ void itp_destroy(itp_handle h) {
     cudaEventDestroy(e.start);
     cudaEventDestroy(e.stop);
   }
+  if (h->own_stream) cudaStreamDestroy(h->st);
   delete h;
 }
 
@@ -797,6 +845,68 @@ int itp_energies(itp_handle h, double* E_host, int flags) {
   ITP_TRY(check_ready(h, true));
   h->have_phi = false;
   return do_energies(h, E_host, flags);
+}
+
+int itp_step(itp_handle h, int order, double tau, int flags, double* E_host) {
+  ITP_TRY(check_ready(h, true));
+  if (order < 2 || order > 2 * kMaxTerms || (order & 1))
+    return fail(h, ITP_ERR_ARG, "order must be even, 2..%d (got %d)", 2 * kMaxTerms, order);
+  if (!(tau > 0) || !std::isfinite(tau)) return fail(h, ITP_ERR_ARG, "tau must be > 0");
+  if (flags != 0 && flags != ITP_RITZ_VALUES)
+    return fail(h, ITP_ERR_ARG, "itp_step takes flags 0 or ITP_RITZ_VALUES");
+  const int k = order / 2;
+  int lane;
+  if (h->precision == ITP_MIXED) {
+    ITP_TRY(switch_lane<float>(h));
+    ITP_TRY(step_resources<float>(h, k, tau));
+    lane = 0;
+  } else {
+    ITP_TRY(step_resources<double>(h, k, tau));
+    lane = 1;
+  }
+  if (!h->step_exec || h->step_order != order || h->step_tau != tau ||
+      h->step_flags != flags || h->step_lane != lane) {
+    if (h->step_exec) {
+      cudaGraphExecDestroy(h->step_exec);
+      h->step_exec = nullptr;
+    }
+    ITP_CUDA(h, cudaStreamSynchronize(h->st));
+    cudaGraph_t graph = nullptr;
+    ITP_CUDA(h, cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
+    h->capturing = true;
+    const long long launches0 = h->launches;
+    const int rc = lane == 0 ? step_work<float>(h, k, tau, flags)
+                             : step_work<double>(h, k, tau, flags);
+    h->capturing = false;
+    h->step_launches = h->launches - launches0;
+    h->launches = launches0;
+    const cudaError_t ec = cudaStreamEndCapture(h->st, &graph);
+    if (rc != ITP_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    ITP_CUDA(h, ec);
+    const cudaError_t ei = cudaGraphInstantiate(&h->step_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    ITP_CUDA(h, ei);
+    h->step_order = order;
+    h->step_tau = tau;
+    h->step_flags = flags;
+    h->step_lane = lane;
+  }
+  ITP_CUDA(h, cudaGraphLaunch(h->step_exec, h->st));
+  h->launches += h->step_launches;
+  h->have_phi = false;
+  ITP_CUDA(h, cudaStreamSynchronize(h->st));
+  const int st = *h->status_host;
+  if (st) {
+    ITP_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->st));
+    if (st & 1) return fail(h, ITP_ERR_NOT_PD, "overlap matrix is not positive definite");
+    if (st & 2) return fail(h, ITP_ERR_NOCONV, "Jacobi eigensolver did not converge");
+    if (st & 4) return fail(h, ITP_ERR_TIMEOUT, "a bounded tensor-core pipeline wait expired");
+  }
+  if (E_host) memcpy(E_host, h->E_host_pinned, h->m * sizeof(double));
+  return ITP_OK;
 }
 
 int itp_polish(itp_handle h, int order, double tau, double tol, int max_steps, int* steps_out,

@@ -43,6 +43,7 @@ SIGNATURES = [
     ("itp_propagate", _I, [_H, _I, _D]),
     ("itp_orthonormalize", _I, [_H]),
     ("itp_energies", _I, [_H, _PD, _I]),
+    ("itp_step", _I, [_H, _I, _D, _I, _PD]),
     ("itp_polish", _I, [_H, _I, _D, _D, _I, ctypes.POINTER(_I), _PD]),
     ("itp_synchronize", _I, [_H]),
     ("itp_last_error", ctypes.c_char_p, [_H]),
@@ -151,6 +152,12 @@ def itp_energies(h, out: np.ndarray | None, flags: int = ITP_RITZ):
     return out
 
 
+def itp_step(h, order, tau, flags=ITP_RITZ_VALUES, out: np.ndarray | None = None):
+    ptr = None if out is None else out.ctypes.data
+    _check(h, load().itp_step(h, int(order), float(tau), int(flags), ptr))
+    return out
+
+
 def itp_polish(h, order, tau, tol, max_steps, out: np.ndarray | None = None):
     steps = _I(0)
     ptr = None if out is None else out.ctypes.data
@@ -256,6 +263,12 @@ class ItpGrid:
         self.propagate(order, tau)
         self.orthonormalize()
         return self.energies(ritz)
+
+    def step_graph(self, order, tau, ritz="values"):
+        """One step replayed from a CUDA graph (Ritz values or, with
+        ritz=False, diagonal energies)."""
+        out = np.empty(self.m, dtype=np.float64)
+        return itp_step(self.h, order, tau, ITP_RITZ_VALUES if ritz else 0, out)
 
     def polish(self, order, tau, tol, max_steps):
         out = np.empty(self.m, dtype=np.float64)

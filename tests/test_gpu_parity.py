@@ -156,6 +156,24 @@ def test_itp_sequence_matches_oracle_iterations(ritz):
             assert np.max(np.abs(E - E_ref)) < 1e-11 * np.max(np.abs(E_ref))
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_graph_step_matches_plain_steps(prec):
+    """itp_step replays the same kernels from a CUDA graph: the energies of
+    every step equal those of the plain call sequence, also across a change
+    of tau (which captures a new graph)."""
+    g = GRIDS[2]
+    V = wells_problem(g)
+    m = 6
+    psi = seeded_states(g, m)
+    plan = [(8, 0.3)] * 3 + [(8, 0.2)] * 2
+    with _grid_handle(g, m, prec, V, psi) as a, _grid_handle(g, m, prec, V, psi) as b:
+        for order, tau in plan:
+            Ea = a.step(order, tau, ritz="values")
+            Eb = b.step_graph(order, tau)
+            assert np.max(np.abs(Ea - Eb)) <= 1e-13 * np.max(np.abs(Ea))
+        assert _relerr(b.get_states(), a.get_states()) < 1e-12
+
+
 def test_not_positive_definite_is_reported():
     g = GRIDS[0]
     V = wells_problem(g)
