@@ -143,12 +143,14 @@ struct PlaneGeo {
   AxisT<NX> ax;
   AxisT<NY> ay;
   int nx, ny, nxh, npair, pp;
+  int gpair;   // row-pair stride of the global (transposed) real layout
   __device__ __forceinline__ PlaneGeo(const GridDesc& g)
       : ax(g.nx, g.rx1, g.rx2), ay(g.ny, g.ry1, g.ry2) {
     nx = NX ? NX : g.nx;
     ny = NY ? NY : g.ny;
     nxh = nx / 2 + 1;
     npair = ny / 2;
+    gpair = npair;
     pp = NX ? row_pitch(NX) : g.pp;
   }
   // x rows: transform t = row pair, element e = x (padded)
@@ -173,8 +175,8 @@ __device__ __forceinline__ void xA_fwd_global_r(const PlaneGeo<R, NX, NY>& G, C*
 #pragma unroll
     for (int j = 0; j < R2; ++j) {
       const int x = n1 + G.ax.r1 * j;
-      a[j] = src[x * G.npair + t];
-      if (f) a[j] = cmulri(a[j], __ldg(&f[x * G.npair + t]));
+      a[j] = src[x * G.gpair + t];
+      if (f) a[j] = cmulri(a[j], __ldg(&f[x * G.gpair + t]));
     }
     Dft<R2, -1, C>::run(a);
     if (G.ax.r1 > 1) {
@@ -586,6 +588,47 @@ struct EpiCombine {
     return false;
   }
 };
+// PLANE_COMBINE on planes that need split passes, mixed path: the running
+// sum is an unevaluated pair (s, e) of FP32 values per point kept in the
+// accumulator buffer and updated with the error-free TwoSum (Knuth), so the
+// sum of the terms' FP32 contributions stays exact up to its final rounding.
+__device__ __forceinline__ void two_sum_acc(float& s, float& e, float x) {
+  const float t = s + x;
+  const float bb = t - s;
+  e += (s - (t - bb)) + (x - bb);
+  s = t;
+}
+template <typename R>
+struct EpiCombinePair {
+  using C = typename CplxOf<R>::type;
+  const C* f;
+  float4* acc;   // per real pair: (s_re, e_re, s_im, e_im)
+  C* phi;
+  float c;
+  int init, npair, r1;
+  template <int R2> __device__ __forceinline__ bool apply(int t, int n1, C* a) const {
+#pragma unroll
+    for (int j = 0; j < R2; ++j) {
+      const int idx = (n1 + r1 * j) * npair + t;
+      const C fv = __ldg(&f[idx]);
+      const float vx = c * ((float)a[j].x * (float)fv.x);
+      const float vy = c * ((float)a[j].y * (float)fv.y);
+      float4 q = init ? make_float4(0.f, 0.f, 0.f, 0.f) : acc[idx];
+      two_sum_acc(q.x, q.y, vx);
+      two_sum_acc(q.z, q.w, vy);
+      if (phi) {
+        C w;
+        w.x = (R)(q.x + q.y);
+        w.y = (R)(q.z + q.w);
+        phi[idx] = w;
+      } else {
+        acc[idx] = q;
+      }
+    }
+    return false;
+  }
+};
+
 // PLANE_TERM: the term's scaled contribution c * f_out * u, rounded to
 // precision R, written over the term's own spectrum plane (its real plane
 // fits in the half-spectrum plane; all of the plane was read before).
@@ -786,6 +829,159 @@ __device__ __forceinline__ void pencil_invA_r(nt_tag<NT>, const C* sm, C* __rest
 }
 
 // ----------------------------------------------------------------------------
+// Split plane passes, for planes whose half spectrum does not fit one CTA's
+// shared memory (nx = ny = 256 in FP32, >= 192 in FP64).  A row pass does
+// the x transform (and the mode's point-wise epilogue) of a block of TB row
+// pairs; column passes do the y transform.  Between them the data is kept
+// in the half-spectrum layout [z][y][kx] with y not yet transformed.
+template <typename R, int NX, int TB>
+struct RowGeo : PlaneGeo<R, NX, 2 * TB> {
+  __device__ __forceinline__ RowGeo(const GridDesc& g) : PlaneGeo<R, NX, 2 * TB>(g) {
+    this->ny = 2 * TB;
+    this->npair = TB;
+    this->gpair = g.ny / 2;
+  }
+};
+
+template <typename R, int NX, int TB, int MODE>
+__global__ void __launch_bounds__(kThreads)
+    rowpass_kernel(const GridDesc g, const PlaneArgs<R> a) {
+  using C = typename CplxOf<R>::type;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const RowGeo<R, NX, TB> G(g);
+  C* sm = reinterpret_cast<C*>(smraw);
+  C* twx = sm + TB * G.pp;
+  for (int i = threadIdx.x; i < G.nx; i += blockDim.x) twx[i] = static_cast<const C*>(a.twx)[i];
+  const int nb = (g.ny / 2) / TB;   // TB divides ny / 2
+  const int z = blockIdx.x / nb, blk = blockIdx.x - z * nb, s = blockIdx.y;
+  const int t0 = blk * TB;
+  const long long plane_pts = (long long)G.nx * g.ny;
+  const long long real_off = (long long)s * g.n_points + (long long)z * plane_pts;
+  const long long fac_off = (long long)z * plane_pts;
+  C* specp = static_cast<C*>(a.spec) + ((long long)s * g.nz + z) * (long long)g.ny * G.nxh;
+  const int rowlen = 2 * G.nxh;
+  __syncthreads();
+
+  if constexpr (MODE == PLANE_FWD_REAL) {
+    const C* src = reinterpret_cast<const C*>(a.in_real + real_off) + t0;
+    const C* f = a.f_in ? reinterpret_cast<const C*>(a.f_in + fac_off) + t0 : nullptr;
+    xA_fwd_global(G, sm, src, f, twx);
+    __syncthreads();
+  } else {
+    // rows y = 2(t0+t) + h of the y-inverted intermediate -> row pair t
+    for (int idx = threadIdx.x; idx < TB * rowlen; idx += blockDim.x) {
+      const int t = idx / rowlen, rem = idx - t * rowlen;
+      sm[t * G.pp + rem] = specp[(long long)(2 * t0) * G.nxh + idx];
+    }
+    __syncthreads();
+    xB_inv_merge(G, sm, twx);
+    __syncthreads();
+    if constexpr (MODE == PLANE_MERGED) {
+      EpiMerged<R> epi{reinterpret_cast<const C*>(a.f_mid + fac_off) + t0, G.gpair, G.ax.r1};
+      xA_inv_then(G, sm, twx, epi);
+      __syncthreads();
+    } else if constexpr (MODE == PLANE_COMBINE) {
+      if constexpr (sizeof(R) == 4) {
+        EpiCombinePair<R> epi{reinterpret_cast<const C*>(a.f_out + fac_off) + t0,
+                              reinterpret_cast<float4*>(a.acc + real_off) + t0,
+                              a.phi_out ? reinterpret_cast<C*>(a.phi_out + real_off) + t0 : nullptr,
+                              (float)a.coef, a.acc_init, G.gpair, G.ax.r1};
+        xA_inv_then(G, sm, twx, epi);
+      } else {
+        EpiCombine<R> epi{reinterpret_cast<const C*>(a.f_out + fac_off) + t0,
+                          reinterpret_cast<double2*>(a.acc + real_off) + t0,
+                          a.phi_out ? reinterpret_cast<C*>(a.phi_out + real_off) + t0 : nullptr,
+                          a.coef, a.acc_init, G.gpair, G.ax.r1};
+        xA_inv_then(G, sm, twx, epi);
+      }
+      return;
+    } else if constexpr (MODE == PLANE_HPSI) {
+      EpiHpsi<R> epi{reinterpret_cast<const C*>(a.in_real + real_off) + t0,
+                     reinterpret_cast<const double2*>(a.V + fac_off) + t0,
+                     reinterpret_cast<double2*>(a.acc + real_off) + t0,
+                     a.V_r ? reinterpret_cast<const C*>(a.V_r + fac_off) + t0 : nullptr,
+                     a.phi_out ? reinterpret_cast<C*>(a.phi_out + real_off) + t0 : nullptr,
+                     G.gpair, G.ax.r1};
+      xA_inv_then(G, sm, twx, epi);
+      return;
+    } else {
+      return;   // PLANE_TERM is not used with split passes
+    }
+  }
+  xB_fwd_split(G, sm, twx);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < TB * rowlen; idx += blockDim.x) {
+    const int t = idx / rowlen, rem = idx - t * rowlen;
+    specp[(long long)(2 * t0) * G.nxh + idx] = sm[t * G.pp + rem];
+  }
+}
+
+// Column pass: the y transform of a block of kx columns of one plane (same
+// slab structure as the pencil pass, along y).
+template <int R1, typename C, int NT>
+__device__ __forceinline__ void col_fwdB_store_r(nt_tag<NT>, const C* sm, C* __restrict__ base,
+                                                 long long rstride, int w, int pw, int r2) {
+  for_tasks<NT>(pw, r2, [&](int t, int b) {
+    if (t >= w) return;
+    C v[R1];
+#pragma unroll
+    for (int i = 0; i < R1; ++i) v[i] = sm[(i + R1 * b) * pw + t];
+    Dft<R1, -1, C>::run(v);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) base[(b + r2 * k1) * rstride + t] = v[k1];
+  });
+}
+template <int R1, typename C, int NT>
+__device__ __forceinline__ void col_invB_load_r(nt_tag<NT>, C* sm, const C* __restrict__ base,
+                                                const C* tw, long long rstride, int w, int pw,
+                                                int r2) {
+  for_tasks<NT>(pw, r2, [&](int t, int b) {
+    if (t >= w) return;
+    C v[R1];
+#pragma unroll
+    for (int i = 0; i < R1; ++i) v[i] = base[(b + r2 * i) * rstride + t];
+    Dft<R1, 1, C>::run(v);
+    if (R1 > 1) {
+#pragma unroll
+      for (int i = 1; i < R1; ++i) v[i] = cmulc(v[i], tw[i * b]);
+    }
+#pragma unroll
+    for (int i = 0; i < R1; ++i) sm[(i + R1 * b) * pw + t] = v[i];
+  });
+}
+
+template <typename R, int NY, int W, int DIR>
+__global__ void __launch_bounds__(launch_threads(task_threads(W)))
+    colpass_kernel(const GridDesc g, void* spec, const void* twy_g, int pw_rt) {
+  constexpr int NT = task_threads(W);
+  using C = typename CplxOf<R>::type;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const AxisT<NY> ay(g.ny, g.ry1, g.ry2);
+  const int ny = NY ? NY : g.ny;
+  const int pw = W ? W : pw_rt;
+  C* twy = sm + ny * pw;
+  for (int i = threadIdx.x; i < ny; i += blockDim.x) twy[i] = static_cast<const C*>(twy_g)[i];
+  const long long plane = blockIdx.y;
+  const int kx0 = blockIdx.x * pw;
+  const int w = min(pw, g.nxh - kx0);
+  C* base = static_cast<C*>(spec) + plane * (long long)ny * g.nxh + kx0;
+  __syncthreads();
+  if constexpr (DIR < 0) {
+    ITP_WITH_RADIX(ay.r2, pencil_fwdA_r, nt_tag<NT>(), sm, base, twy, (long long)g.nxh, w, pw,
+                   ay.r1)
+    __syncthreads();
+    ITP_WITH_RADIX(ay.r1, col_fwdB_store_r, nt_tag<NT>(), sm, base, (long long)g.nxh, w, pw,
+                   ay.r2)
+  } else {
+    ITP_WITH_RADIX(ay.r1, col_invB_load_r, nt_tag<NT>(), sm, base, twy, (long long)g.nxh, w, pw,
+                   ay.r2)
+    __syncthreads();
+    ITP_WITH_RADIX(ay.r2, pencil_invA_r, nt_tag<NT>(), sm, base, (long long)g.nxh, w, pw, ay.r1)
+  }
+}
+
+// ----------------------------------------------------------------------------
 // Pencil pass.  Slab element (z, column t) at shared position z * W + t.
 template <typename R, int NZ, int W, int MODE>
 __global__ void __launch_bounds__(launch_threads(task_threads(W)),
@@ -854,17 +1050,11 @@ __global__ void term_tables_kernel(const GridDesc g, const double* __restrict__ 
 
 // phi[s][z][:] = sum_i term_i[s][z][:] in FP64, rounded to FP32; term_i is
 // stored with the half-spectrum plane pitch (in floats).
-// Error-free sum of FP32 values (Knuth's TwoSum): s + e carries the running
-// sum with no rounding error beyond the compensation term, so the result is
-// the exact sum of the contributions up to its final rounding to FP32.  On
-// this GPU the FP64 pipe runs at a small fraction of the FP32 rate, and a
-// plain FP64 sum with its conversions costs an order of magnitude more.
-__device__ __forceinline__ void two_sum_acc(float& s, float& e, float x) {
-  const float t = s + x;
-  const float bb = t - s;
-  e += (s - (t - bb)) + (x - bb);
-  s = t;
-}
+// term_sum_kernel sums with two_sum_acc (error-free TwoSum, defined with the
+// epilogues): the result is the exact sum of the FP32 contributions up to its
+// final rounding.  On this GPU the FP64 pipe runs at a small fraction of the
+// FP32 rate, and a plain FP64 sum with its conversions costs an order of
+// magnitude more.
 
 __global__ void term_sum_kernel(const TermSumArgs a) {
   // blockIdx.y = plane (state, z); x-blocks stride over the plane's float4s
@@ -970,8 +1160,85 @@ size_t pencil_smem_bytes(const GridDesc& g, int real_bytes) {
   return ((size_t)g.nz * g.pencil_w + g.nz) * 2 * real_bytes;
 }
 
+template <typename R, int NX, int TB>
+cudaError_t rowpass_dispatch(const GridDesc& g, const PlaneArgs<R>& a, cudaStream_t st) {
+  const size_t smem = ((size_t)TB * g.pp + g.nx) * 2 * sizeof(R);
+  dim3 grid(g.nz * ((g.ny / 2) / TB), a.m);
+  cudaError_t e;
+  switch (a.mode) {
+#define ITP_ROW_CASE(M)                                                     \
+  case M:                                                                   \
+    e = set_smem(rowpass_kernel<R, NX, TB, M>, smem);                       \
+    if (e != cudaSuccess) return e;                                         \
+    rowpass_kernel<R, NX, TB, M><<<grid, kThreads, smem, st>>>(g, a);       \
+    break;
+    ITP_ROW_CASE(PLANE_FWD_REAL)
+    ITP_ROW_CASE(PLANE_MERGED)
+    ITP_ROW_CASE(PLANE_COMBINE)
+    ITP_ROW_CASE(PLANE_HPSI)
+#undef ITP_ROW_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 template <typename R>
-cudaError_t launch_plane(const GridDesc& g, const PlaneArgs<R>& a, cudaStream_t st) {
+cudaError_t rowpass_launch(const GridDesc& g, const PlaneArgs<R>& a, cudaStream_t st) {
+  const int tb = g.row_tb[sizeof(R) == 4 ? 0 : 1];
+  if (g.nx == 256 && g.pp == row_pitch(256) && tb == (sizeof(R) == 4 ? 32 : 16)) {
+    if constexpr (sizeof(R) == 4) return rowpass_dispatch<R, 256, 32>(g, a, st);
+    else return rowpass_dispatch<R, 256, 16>(g, a, st);
+  }
+  if (tb == 32) return rowpass_dispatch<R, 0, 32>(g, a, st);
+  if (tb == 16) return rowpass_dispatch<R, 0, 16>(g, a, st);
+  if (tb == 8) return rowpass_dispatch<R, 0, 8>(g, a, st);
+  return cudaErrorInvalidValue;
+}
+
+template <typename R, int NY, int W, int DIR>
+cudaError_t colpass_one(const GridDesc& g, void* spec, const void* twy, int m, cudaStream_t st) {
+  const int cw = g.col_w[sizeof(R) == 4 ? 0 : 1];
+  const size_t smem = ((size_t)g.ny * cw + g.ny) * 2 * sizeof(R);
+  cudaError_t e = set_smem(colpass_kernel<R, NY, W, DIR>, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((g.nxh + cw - 1) / cw, (unsigned)((long long)m * g.nz));
+  colpass_kernel<R, NY, W, DIR><<<grid, launch_threads(task_threads(W)), smem, st>>>(
+      g, spec, twy, cw);
+  return cudaGetLastError();
+}
+
+template <typename R, int DIR>
+cudaError_t colpass_launch(const GridDesc& g, void* spec, const void* twy, int m, cudaStream_t st) {
+  if (g.ny == 256 && g.col_w[sizeof(R) == 4 ? 0 : 1] == (sizeof(R) == 4 ? 33 : 17)) {
+    if constexpr (sizeof(R) == 4) return colpass_one<R, 256, 33, DIR>(g, spec, twy, m, st);
+    else return colpass_one<R, 256, 17, DIR>(g, spec, twy, m, st);
+  }
+  return colpass_one<R, 0, 0, DIR>(g, spec, twy, m, st);
+}
+
+template <typename R>
+cudaError_t launch_plane(const GridDesc& g, const PlaneArgs<R>& a, cudaStream_t st, int* nlaunch) {
+  if (nlaunch) *nlaunch = 1;
+  if (g.split_planes[sizeof(R) == 4 ? 0 : 1]) {
+    // planes too large for one CTA: column passes for y, row passes for x
+    cudaError_t e = cudaSuccess;
+    int n = 0;
+    if (a.mode != PLANE_FWD_REAL) {
+      e = colpass_launch<R, 1>(g, a.spec, a.twy, a.m, st);
+      ++n;
+      if (e != cudaSuccess) return e;
+    }
+    e = rowpass_launch<R>(g, a, st);
+    ++n;
+    if (e != cudaSuccess) return e;
+    if (a.mode == PLANE_FWD_REAL || a.mode == PLANE_MERGED) {
+      e = colpass_launch<R, -1>(g, a.spec, a.twy, a.m, st);
+      ++n;
+    }
+    if (nlaunch) *nlaunch = n;
+    return e;
+  }
   const size_t smem = plane_smem_bytes(g, sizeof(R));
   if (g.nx == g.ny && g.pp == row_pitch(g.nx)) {
     switch (g.nx) {
@@ -1038,8 +1305,10 @@ cudaError_t launch_transpose_planes(const TS* src, TD* dst, long long nplanes, i
   return cudaGetLastError();
 }
 
-template cudaError_t launch_plane<float>(const GridDesc&, const PlaneArgs<float>&, cudaStream_t);
-template cudaError_t launch_plane<double>(const GridDesc&, const PlaneArgs<double>&, cudaStream_t);
+template cudaError_t launch_plane<float>(const GridDesc&, const PlaneArgs<float>&, cudaStream_t,
+                                         int*);
+template cudaError_t launch_plane<double>(const GridDesc&, const PlaneArgs<double>&, cudaStream_t,
+                                          int*);
 template cudaError_t launch_pencil<float>(const GridDesc&, const PencilArgs<float>&, cudaStream_t);
 template cudaError_t launch_pencil<double>(const GridDesc&, const PencilArgs<double>&, cudaStream_t);
 template cudaError_t launch_term_tables<float>(const GridDesc&, const double*, double, double,

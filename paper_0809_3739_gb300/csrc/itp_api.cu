@@ -261,6 +261,15 @@ void free_lane(Lane<R>& L) {
   L = Lane<R>();
 }
 
+// A plane pass: 1 kernel, or 2-3 kernels on split planes (counted).
+template <typename R>
+cudaError_t plane_counted(itp_handle h, const PlaneArgs<R>& a) {
+  int n = 1;
+  const cudaError_t e = launch_plane<R>(h->g, a, h->st, &n);
+  h->launches += n - 1;
+  return e;
+}
+
 template <typename R>
 Lane<R>& lane_of(itp_handle h);
 template <>
@@ -297,7 +306,7 @@ int propagate_lane(itp_handle h, int k, double tau) {
   ITP_TRY(prepare_tables<R>(h, L, k, tau));
   const GridDesc& g = h->g;
   const size_t tl = (size_t)g.nxh + g.ny + g.nz;
-  bool fused = sizeof(R) == 4 && L.fused_ok;
+  bool fused = sizeof(R) == 4 && L.fused_ok && !g.split_planes[0];
   if (fused) {
     L.work_terms[0] = L.work;
     for (int i = 1; i < k && fused; ++i) {
@@ -319,7 +328,7 @@ int propagate_lane(itp_handle h, int k, double tau) {
     pa.twy = L.twy;
     pa.mode = PLANE_FWD_REAL;
     pa.f_in = L.f_half[i - 1];
-    ITP_LAUNCH(h, ITP_KERNEL_PLANE_FWD, launch_plane<R>(g, pa, h->st));
+    ITP_LAUNCH(h, ITP_KERNEL_PLANE_FWD, plane_counted<R>(h, pa));
     PencilArgs<R> pe{};
     pe.mode = PENCIL_PROPAGATE;
     pe.m = h->m;
@@ -337,7 +346,7 @@ int propagate_lane(itp_handle h, int k, double tau) {
         pm.mode = PLANE_MERGED;
         pm.f_in = nullptr;
         pm.f_mid = L.f_full[i - 1];
-        ITP_LAUNCH(h, ITP_KERNEL_PLANE_MERGED, launch_plane<R>(g, pm, h->st));
+        ITP_LAUNCH(h, ITP_KERNEL_PLANE_MERGED, plane_counted<R>(h, pm));
       }
     }
     if (fused) {
@@ -347,7 +356,7 @@ int propagate_lane(itp_handle h, int k, double tau) {
       pt.f_in = nullptr;
       pt.f_out = L.f_half[i - 1];
       pt.coef = mp_coefficient(i, k);
-      ITP_LAUNCH(h, ITP_KERNEL_PLANE_COMBINE, launch_plane<R>(g, pt, h->st));
+      ITP_LAUNCH(h, ITP_KERNEL_PLANE_COMBINE, plane_counted<R>(h, pt));
       ts.term[i - 1] = reinterpret_cast<const float*>(work);
       continue;
     }
@@ -360,7 +369,7 @@ int propagate_lane(itp_handle h, int k, double tau) {
     pc.acc_init = (i == 1);
     // the mixed path keeps the sum in FP64 and rounds the finished phi once
     pc.phi_out = (sizeof(R) == 4 && i == k) ? L.psi_tmp : nullptr;
-    ITP_LAUNCH(h, ITP_KERNEL_PLANE_COMBINE, launch_plane<R>(g, pc, h->st));
+    ITP_LAUNCH(h, ITP_KERNEL_PLANE_COMBINE, plane_counted<R>(h, pc));
   }
   if (fused) {
     // phi = sum_i c_i f u_i in FP64 over the FP32 contributions
@@ -421,7 +430,7 @@ int energies_lane(itp_handle h, int flags) {
   pa.twy = L.twy;
   pa.mode = PLANE_FWD_REAL;
   pa.f_in = nullptr;
-  ITP_LAUNCH(h, ITP_KERNEL_PLANE_FWD, launch_plane<R>(g, pa, h->st));
+  ITP_LAUNCH(h, ITP_KERNEL_PLANE_FWD, plane_counted<R>(h, pa));
   PencilArgs<R> pe{};
   pe.mode = PENCIL_KINETIC;
   pe.m = h->m;
@@ -441,7 +450,7 @@ int energies_lane(itp_handle h, int flags) {
     ph.V_r = L.Vr;
     ph.phi_out = L.psi_tmp;
   }
-  ITP_LAUNCH(h, ITP_KERNEL_PLANE_HPSI, launch_plane<R>(g, ph, h->st));
+  ITP_LAUNCH(h, ITP_KERNEL_PLANE_HPSI, plane_counted<R>(h, ph));
   if (sizeof(R) == 4) {
     ITP_LAUNCH(h, ITP_KERNEL_GRAM, (launch_tc_gram(
                                        reinterpret_cast<const float*>(L.psi),
@@ -556,7 +565,7 @@ template <typename R>
 int step_resources(itp_handle h, int k, double tau) {
   Lane<R>& L = lane_of<R>(h);
   ITP_TRY(prepare_tables<R>(h, L, k, tau));
-  if (sizeof(R) == 4 && L.fused_ok) {
+  if (sizeof(R) == 4 && L.fused_ok && !h->g.split_planes[0]) {
     L.work_terms[0] = L.work;
     for (int i = 1; i < k; ++i) {
       if (!L.work_terms[i] &&
@@ -617,12 +626,29 @@ int itp_create_grid(itp_handle* out, int nx, int ny, int nz, double lx, double l
     g.pencil_w = (g.nxh + chunks - 1) / chunks;
     g.pencil_pitch = g.pencil_w;
   }
-  const size_t plane_bytes = plane_smem_bytes(g, cbytes / 2);
-  size_t plane64 = plane_smem_bytes(g, 8);
-  if (plane_bytes > kSmemLimit || (precision == ITP_MIXED && plane64 > kSmemLimit))
-    return bail(fail(h, ITP_ERR_ARG, "a %dx%d plane needs %zu bytes of shared memory "
-                                     "(limit %zu)", nx, ny,
-                     precision == ITP_MIXED ? plane64 : plane_bytes, kSmemLimit));
+  // planes whose half spectrum does not fit one CTA run as row + column
+  // passes: row-pass blocks of tb row pairs, column-pass blocks of cw columns
+  for (int pi = 0; pi < 2; ++pi) {
+    const int rb = pi == 0 ? 4 : 8;   // bytes per real
+    g.split_planes[pi] = plane_smem_bytes(g, rb) > kSmemLimit;
+    g.row_tb[pi] = 0;
+    g.col_w[pi] = 0;
+    if (!g.split_planes[pi]) continue;
+    for (int tb : {32, 16, 8}) {
+      if ((ny / 2) % tb == 0 && ((size_t)tb * g.pp + nx) * 2 * rb <= 96 * 1024 &&
+          (tb != 32 || (pi == 0 && nx == 256))) {
+        g.row_tb[pi] = tb;
+        break;
+      }
+    }
+    const size_t budget = 72 * 1024, full = (size_t)ny * g.nxh * 2 * rb;
+    const int chunks = (int)((full + budget - 1) / budget);
+    g.col_w[pi] = (g.nxh + chunks - 1) / chunks;
+  }
+  const int need = precision == ITP_MIXED ? 2 : 1;
+  for (int pi = (precision == ITP_MIXED ? 0 : 1); pi < 2 && need; ++pi)
+    if (g.split_planes[pi] && g.row_tb[pi] == 0)
+      return bail(fail(h, ITP_ERR_ARG, "no row-pass blocking for a %dx%d plane", nx, ny));
   h->lx = lx;
   h->ly = ly;
   h->lz = lz;

@@ -15,6 +15,11 @@ struct GridDesc {
   int pp;                    // shared-memory pitch of a row pair (complex, odd)
   int pencil_w;              // kx columns per pencil CTA
   int pencil_pitch;          // shared-memory pitch of a pencil z-row (complex)
+  // planes too large for one CTA run as row + column passes; per precision
+  // (index 0: FP32, 1: FP64)
+  int split_planes[2];
+  int row_tb[2];             // row pairs per row-pass CTA
+  int col_w[2];              // kx columns per column-pass CTA
 };
 
 // Pass kinds.
@@ -81,8 +86,11 @@ size_t plane_smem_bytes(const GridDesc& g, int real_bytes);
 int plane_row_pitch(int nx);   // odd pitch (complex) of a row pair in shared memory
 size_t pencil_smem_bytes(const GridDesc& g, int real_bytes);
 
+// One plane pass (*nlaunch receives the number of kernels: 1, or 2-3 when
+// the planes are split into row and column passes).
 template <typename R>
-cudaError_t launch_plane(const GridDesc& g, const PlaneArgs<R>& a, cudaStream_t st);
+cudaError_t launch_plane(const GridDesc& g, const PlaneArgs<R>& a, cudaStream_t st,
+                         int* nlaunch = nullptr);
 template <typename R>
 cudaError_t launch_pencil(const GridDesc& g, const PencilArgs<R>& a, cudaStream_t st);
 
