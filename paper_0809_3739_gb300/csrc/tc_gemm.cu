@@ -203,6 +203,12 @@ constexpr int kGramKT = 32;                          // points per tile
 constexpr int kGramKC = kGramKT / 4;                 // 4-element K chunks
 constexpr int kTileBytes = 128 * kGramKT * 4;        // 16 KB per operand part
 
+// The tensor core's FP32 accumulation in TMEM is not round-to-nearest: summed
+// over a chunk of ~10^5 points (thousands of accumulating MMAs) the diagonal
+// of S came out low by ~1e-3 relative.  So every tile gets a fresh TMEM
+// accumulator (two, alternating), and the threads add each finished tile
+// into FP32 registers, where rounding is to nearest: 64 entries per thread.
+//
 // Raw tiles (128 state rows x 32 points, FP32) arrive by one 2D TMA load
 // per operand into a ring of RAW stages, 128-byte swizzled: 16-byte chunk c
 // of row r sits at chunk position c ^ (r % 8), so the converters' column
@@ -237,11 +243,27 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     mbar_init(&mma_done[1], 1);
     fence_barrier_init();
   }
-  if (warp == 0) tmem_alloc(&tmem_base, 128);
+  if (warp == 0) tmem_alloc(&tmem_base, 256);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
+
+  // warp w reads TMEM lane quadrant w % 4; warps 4.. take the upper column halves
+  const int quad = warp & 3, chalf = warp >> 2;
+  float acc[64];
+#pragma unroll
+  for (int q = 0; q < 64; ++q) acc[q] = 0.f;
+  auto drain = [&](int c) {   // all threads: acc += accumulator c
+#pragma unroll
+    for (int cc = 0; cc < 2; ++cc) {
+      uint32_t rr[32];
+      tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * 128 + (chalf * 2 + cc) * 32),
+                rr);
+#pragma unroll
+      for (int q = 0; q < 32; ++q) acc[cc * 32 + q] += __uint_as_float(rr[q]);
+    }
+  };
 
   const long long p_begin = (long long)blockIdx.x * chunk;
   const long long p_end = min(N, p_begin + chunk);
@@ -261,7 +283,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   for (int t = 0; t < ntiles; ++t) {
     const int r = t % RAW, c = t & 1;
     mbar_wait(&full[r], (uint32_t)((t / RAW) & 1), status);
-    if (t >= 2) mbar_wait(&mma_done[c], (uint32_t)(((t - 2) >> 1) & 1), status);
+    if (t >= 2) {   // tile t-2 is done: its stage and accumulator are free
+      mbar_wait(&mma_done[c], (uint32_t)(((t - 2) >> 1) & 1), status);
+      tc_fence_after();
+      drain(c);
+    }
 #pragma unroll
     for (int op = 0; op < NOPS; ++op) {
       const unsigned char* rp = sgen + raw_off + (r * NOPS + op) * kRawBytes;
@@ -296,44 +322,36 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const uint64_t dal = smem_desc(alo + koff, 128, sbo);
         const uint64_t dbh = smem_desc(bhi + koff, 128, sbo);
         const uint64_t dbl = smem_desc(blo + koff, 128, sbo);
-        mma_tf32(tmem, dah, dbh, idesc, (t > 0 || ks > 0) ? 1u : 0u);
-        mma_tf32(tmem, dah, dbl, idesc, 1u);
-        mma_tf32(tmem, dal, dbh, idesc, 1u);
+        const uint32_t d = tmem + (uint32_t)(c * 128);
+        mma_tf32(d, dah, dbh, idesc, ks > 0 ? 1u : 0u);
+        mma_tf32(d, dah, dbl, idesc, 1u);
+        mma_tf32(d, dal, dbh, idesc, 1u);
       }
       mma_commit(&mma_done[c]);
       // raw slot r was consumed by every thread before the barrier above
       if (t + RAW < ntiles) issue(t + RAW, r);
     }
   }
-  double* out = partial + (long long)blockIdx.x * m * m;
-  if (ntiles > 0) {
-    const int tl = ntiles - 1;
+  // the last two tiles are not drained yet
+  for (int tl = ntiles >= 2 ? ntiles - 2 : 0; tl < ntiles; ++tl) {
     mbar_wait(&mma_done[tl & 1], (uint32_t)((tl >> 1) & 1), status);
     tc_fence_after();
-    // warp w reads TMEM lane quadrant w % 4; warps 4.. take the upper column halves
-    const int quad = warp & 3, chalf = warp >> 2;
-    const int i = quad * 32 + lane;
+    drain(tl & 1);
+  }
+  double* out = partial + (long long)blockIdx.x * m * m;
+  const int i = quad * 32 + lane;
+  if (i < m) {
 #pragma unroll
-    for (int cc = 0; cc < 2; ++cc) {
-      const int cb = chalf * 2 + cc;
-      uint32_t rr[32];
-      tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cb * 32), rr);
-      if (i < m) {
-#pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          const int j = cb * 32 + q;
-          if (j < m) out[(long long)i * m + j] = (double)__uint_as_float(rr[q]);
-        }
-      }
+    for (int q = 0; q < 64; ++q) {
+      const int j = chalf * 64 + q;
+      if (j < m) out[(long long)i * m + j] = (double)acc[q];
     }
-  } else {
-    for (int e = threadIdx.x; e < m * m; e += kTcThreads) out[e] = 0.0;
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tmem, 128);
+    tmem_dealloc(tmem, 256);
   }
 }
 

@@ -73,3 +73,21 @@ def test_c60_256_cubed_sampled():
     # L^{-1} amplifies the error of phi by up to sqrt(cond(S)) of the block
     kappa = np.sqrt(np.linalg.cond(O.overlap(phi_ref, g.dV)))
     assert _relerr(got, psi_ref) < 2 * tol * kappa
+
+
+def test_mixed_overlap_long_chunks():
+    """Orthonormalised FP32 states over 256^3 points: each tensor-core CTA
+    sums ~10^5 points of the overlap (Eq. 4's S), and psi^T psi dV must come
+    out as the identity to FP32 accuracy, not to the tensor core's
+    accumulation error."""
+    g = cubic(256, 32.0)
+    m = 8
+    psi = normal_states(m, g.n_points, seed=99)
+    with P.ItpGrid(256, 256, 256, 32.0, 32.0, 32.0, m, 0, P.ITP_MIXED) as h:
+        h.set_potential(np.zeros(g.n_points))
+        h.set_states(psi)
+        h.propagate(2, 1e-3)   # orthonormalisation works on the propagated block
+        h.orthonormalize()
+        got = h.get_states()
+    S = got @ got.T * g.dV
+    assert np.max(np.abs(S - np.eye(m))) < 1e-5
