@@ -183,6 +183,62 @@ int itp_profile(itp_handle h, int enable);
  * the last itp_profile call.  Synchronises. */
 int itp_profile_read(itp_handle h, int kind, long long* launches, double* total_ms);
 
+/* ---- Batches of independent problems ----------------------------------------
+ * Many independent problems of uneven size -- each with its own grid,
+ * potential and state count -- advanced together.  The paper treats one
+ * problem at a time; a batch takes exactly the per-problem steps of Eqs. 3
+ * and 4 (as itp_step), with each problem's step captured as one branch of a
+ * single CUDA graph: one graph launch advances every problem, and the GPU
+ * runs the branches concurrently, so small problems fill the SMs together. */
+typedef struct itp_batch* itp_batch_handle;
+
+/* itp_batch_step flag: mixed-precision problems take this step in FP64 (the
+ * polish steps of the mixed path).  Their states move to FP64 and move back
+ * at the next step without the flag. */
+#define ITP_STEP_FP64 4
+
+/* Create count >= 1 problems.  Problem p has the grid dims[3p..3p+2] =
+ * (nx, ny, nz) and box boxes[3p..3p+2] = (lx, ly, lz) (the rules of
+ * itp_create_grid apply), n_states[p] >= 1 states and n_guard[p] >= 0 guard
+ * states (n_guard NULL: none); precision as itp_create_grid, the same for
+ * all.  Each problem gets a stream of its own; the batch's graph is launched
+ * on cuda_stream (NULL: a stream the batch creates).  On failure *out is
+ * NULL and itp_batch_last_error(NULL) names the problem that failed and
+ * why. */
+int itp_create_batch(itp_batch_handle* out, int count, const int* dims, const double* boxes,
+                     const int* n_states, const int* n_guard, int precision, void* cuda_stream);
+
+/* The handle of problem p (0 <= p < count), owned by the batch: set its
+ * potential and states, read its states and energies with the single-problem
+ * calls; never pass it to itp_destroy.  NULL for a bad index. */
+itp_handle itp_batch_problem(itp_batch_handle b, int p);
+
+/* Number of problems in the batch (0 for NULL). */
+int itp_batch_count(itp_batch_handle b);
+
+/* One step of every problem -- itp_propagate(order, tau),
+ * itp_orthonormalize and energies with flags 0 or ITP_RITZ_VALUES, plus
+ * optionally ITP_STEP_FP64 -- as one CUDA graph launch on the batch's stream.
+ * The first call for a given (order, tau, flags) captures the graph; later
+ * calls replay it.  Every problem needs its potential and states set.
+ * Synchronises.  E_host (nullable) receives all problems' energies back to
+ * back: problem p's m_p = n_states[p] + n_guard[p] values start at
+ * sum_{q<p} m_q.  Returns ITP_OK or the first problem's error
+ * (ITP_ERR_NOT_PD, ITP_ERR_NOCONV, ITP_ERR_TIMEOUT, ...); the message of
+ * itp_batch_last_error names the problem. */
+int itp_batch_step(itp_batch_handle b, int order, double tau, int flags, double* E_host);
+
+/* Kernels launched by the batch's steps so far (graph nodes counted per
+ * replay). */
+long long itp_batch_kernel_launches(itp_batch_handle b);
+
+/* One-line description of the last error on the batch; with b == NULL, why
+ * the calling thread's last itp_create_batch failed. */
+const char* itp_batch_last_error(itp_batch_handle b);
+
+/* Free the batch and every problem handle in it. */
+void itp_batch_destroy(itp_batch_handle b);
+
 /* Orthonormalise a block of states that already lives in device memory,
  * without allocating any device memory: for callers that cannot call
  * cudaMalloc -- code running inside a memory pool or arena that owns all

@@ -582,6 +582,36 @@ int step_resources(itp_handle h, int k, double tau) {
 
 }  // namespace
 
+// A batch of independent problems: one handle (and stream) per problem and
+// the CUDA graph of one step of all of them.
+struct itp_batch {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  std::vector<itp_handle> probs;
+  std::vector<int> e_off;   // offset of problem p's energies
+  int m_total = 0;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraphExec_t exec = nullptr;
+  int order = 0, flags = -1;
+  double tau = 0.0;
+  long long step_launches = 0, launches = 0;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_batch_create_error;
+
+int batch_fail(itp_batch* b, int code, const std::string& msg) {
+  if (b) b->err = msg;
+  else g_batch_create_error = msg;
+  return code;
+}
+
+}  // namespace
+
 extern "C" {
 
 void itp_destroy(itp_handle h);
@@ -1005,6 +1035,182 @@ int itp_profile_read(itp_handle h, int kind, long long* launches, double* total_
   if (launches) *launches = n;
   if (total_ms) *total_ms = ms;
   return ITP_OK;
+}
+
+// ---- batches of independent problems --------------------------------------------
+
+void itp_batch_destroy(itp_batch_handle b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  if (b->st) cudaStreamSynchronize(b->st);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (itp_handle h : b->probs) itp_destroy(h);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (cudaEvent_t e : b->join)
+    if (e) cudaEventDestroy(e);
+  if (b->own_stream) cudaStreamDestroy(b->st);
+  delete b;
+}
+
+int itp_create_batch(itp_batch_handle* out, int count, const int* dims, const double* boxes,
+                     const int* n_states, const int* n_guard, int precision, void* cuda_stream) {
+  if (!out) return ITP_ERR_ARG;
+  *out = nullptr;
+  g_batch_create_error.clear();
+  if (count < 1 || !dims || !boxes || !n_states)
+    return batch_fail(nullptr, ITP_ERR_ARG, "need count >= 1 and non-null dims, boxes, n_states");
+  itp_batch_handle b = new (std::nothrow) itp_batch();
+  if (!b) return ITP_ERR_OOM;
+  auto bail = [&](int code, const std::string& msg) {
+    itp_batch_destroy(b);
+    return batch_fail(nullptr, code, msg);
+  };
+  if (cudaGetDevice(&b->device) != cudaSuccess) return bail(ITP_ERR_CUDA, "no CUDA device");
+  b->st = (cudaStream_t)cuda_stream;
+  if (!b->st) {
+    if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess)
+      return bail(ITP_ERR_CUDA, "cannot create a stream");
+    b->own_stream = true;
+  }
+  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+    return bail(ITP_ERR_CUDA, "cannot create an event");
+  b->probs.assign(count, nullptr);
+  b->join.assign(count, nullptr);
+  b->e_off.assign(count, 0);
+  for (int p = 0; p < count; ++p) {
+    itp_handle h = nullptr;
+    const int rc = itp_create_grid(&h, dims[3 * p], dims[3 * p + 1], dims[3 * p + 2],
+                                   boxes[3 * p], boxes[3 * p + 1], boxes[3 * p + 2], n_states[p],
+                                   n_guard ? n_guard[p] : 0, precision, nullptr);
+    if (rc != ITP_OK)
+      return bail(rc, "problem " + std::to_string(p) + ": " + itp_last_error(nullptr));
+    b->probs[p] = h;
+    b->e_off[p] = b->m_total;
+    b->m_total += h->m;
+    if (cudaEventCreateWithFlags(&b->join[p], cudaEventDisableTiming) != cudaSuccess)
+      return bail(ITP_ERR_CUDA, "cannot create an event");
+  }
+  *out = b;
+  return ITP_OK;
+}
+
+itp_handle itp_batch_problem(itp_batch_handle b, int p) {
+  if (!b || p < 0 || p >= (int)b->probs.size()) return nullptr;
+  return b->probs[p];
+}
+
+int itp_batch_count(itp_batch_handle b) { return b ? (int)b->probs.size() : 0; }
+
+int itp_batch_step(itp_batch_handle b, int order, double tau, int flags, double* E_host) {
+  if (!b) return ITP_ERR_ARG;
+  if (order < 2 || order > 2 * kMaxTerms || (order & 1))
+    return batch_fail(b, ITP_ERR_ARG, "order must be even, 2.." + std::to_string(2 * kMaxTerms));
+  if (!(tau > 0) || !std::isfinite(tau)) return batch_fail(b, ITP_ERR_ARG, "tau must be > 0");
+  const int eflags = flags & ~ITP_STEP_FP64;
+  if (eflags != 0 && eflags != ITP_RITZ_VALUES)
+    return batch_fail(b, ITP_ERR_ARG, "flags: 0 or ITP_RITZ_VALUES, plus ITP_STEP_FP64");
+  if (cudaSetDevice(b->device) != cudaSuccess) return batch_fail(b, ITP_ERR_CUDA, "device");
+  const int k = order / 2;
+  const int np = (int)b->probs.size();
+  auto prob_fail = [&](int p, int rc) {
+    return batch_fail(b, rc, "problem " + std::to_string(p) + ": " + b->probs[p]->err);
+  };
+  // per problem, outside any capture: lane, tables and workspaces
+  for (int p = 0; p < np; ++p) {
+    itp_handle h = b->probs[p];
+    int rc = check_ready(h, true);
+    if (rc == ITP_OK) {
+      if (h->precision == ITP_MIXED && !(flags & ITP_STEP_FP64)) {
+        rc = switch_lane<float>(h);
+        if (rc == ITP_OK) rc = step_resources<float>(h, k, tau);
+      } else {
+        if (h->precision == ITP_MIXED) rc = switch_lane<double>(h);
+        if (rc == ITP_OK) rc = step_resources<double>(h, k, tau);
+      }
+    }
+    if (rc != ITP_OK) return prob_fail(p, rc);
+    // the batch stream must not start the graph before this problem's own work
+    if (cudaEventRecord(b->join[p], h->st) != cudaSuccess ||
+        cudaStreamWaitEvent(b->st, b->join[p], 0) != cudaSuccess)
+      return batch_fail(b, ITP_ERR_CUDA, "stream ordering");
+  }
+  if (!b->exec || b->order != order || b->tau != tau || b->flags != flags) {
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    if (cudaStreamSynchronize(b->st) != cudaSuccess)
+      return batch_fail(b, ITP_ERR_CUDA, "synchronise before capture");
+    if (cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return batch_fail(b, ITP_ERR_CUDA, "begin capture");
+    cudaEventRecord(b->fork, b->st);
+    int rc = ITP_OK, bad = -1;
+    long long n = 0;
+    for (int p = 0; p < np && rc == ITP_OK; ++p) {
+      itp_handle h = b->probs[p];
+      // each problem's stream joins the capture as one branch of the graph
+      if (cudaStreamWaitEvent(h->st, b->fork, 0) != cudaSuccess) {
+        rc = batch_fail(b, ITP_ERR_CUDA, "fork");
+        break;
+      }
+      h->capturing = true;
+      const long long l0 = h->launches;
+      rc = h->cur64 ? step_work<double>(h, k, tau, eflags) : step_work<float>(h, k, tau, eflags);
+      h->capturing = false;
+      n += h->launches - l0;
+      h->launches = l0;
+      if (rc != ITP_OK) {
+        bad = p;
+        break;
+      }
+      if (cudaEventRecord(b->join[p], h->st) != cudaSuccess ||
+          cudaStreamWaitEvent(b->st, b->join[p], 0) != cudaSuccess)
+        rc = batch_fail(b, ITP_ERR_CUDA, "join");
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(b->st, &graph);
+    if (rc != ITP_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return bad >= 0 ? prob_fail(bad, rc) : rc;
+    }
+    if (ec != cudaSuccess)
+      return batch_fail(b, ITP_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(ec));
+    const cudaError_t ei = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess)
+      return batch_fail(b, ITP_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(ei));
+    b->order = order;
+    b->tau = tau;
+    b->flags = flags;
+    b->step_launches = n;
+  }
+  if (cudaGraphLaunch(b->exec, b->st) != cudaSuccess)
+    return batch_fail(b, ITP_ERR_CUDA, "graph launch");
+  b->launches += b->step_launches;
+  if (cudaStreamSynchronize(b->st) != cudaSuccess)
+    return batch_fail(b, ITP_ERR_CUDA, "graph execution failed");
+  int first = ITP_OK;
+  for (int p = 0; p < np; ++p) {
+    itp_handle h = b->probs[p];
+    h->have_phi = false;
+    const int stw = *h->status_host;
+    if (stw) {
+      cudaMemsetAsync(h->status, 0, sizeof(int), h->st);
+      int rc = ITP_OK;
+      if (stw & 1) rc = fail(h, ITP_ERR_NOT_PD, "overlap matrix is not positive definite");
+      else if (stw & 2) rc = fail(h, ITP_ERR_NOCONV, "eigensolver did not converge");
+      else if (stw & 4) rc = fail(h, ITP_ERR_TIMEOUT, "a bounded tensor-core wait expired");
+      if (rc != ITP_OK && first == ITP_OK) first = prob_fail(p, rc);
+    }
+    if (E_host) memcpy(E_host + b->e_off[p], h->E_host_pinned, h->m * sizeof(double));
+  }
+  return first;
+}
+
+long long itp_batch_kernel_launches(itp_batch_handle b) { return b ? b->launches : 0; }
+
+const char* itp_batch_last_error(itp_batch_handle b) {
+  return b ? b->err.c_str() : g_batch_create_error.c_str();
 }
 
 }  // extern "C"

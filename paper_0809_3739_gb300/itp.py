@@ -21,6 +21,7 @@ ITP_FP64 = 0
 ITP_MIXED = 1
 ITP_RITZ = 1
 ITP_RITZ_VALUES = 2
+ITP_STEP_FP64 = 4
 
 _ERR_NAMES = {1: "ITP_ERR_ARG", 2: "ITP_ERR_CUDA", 3: "ITP_ERR_NOT_PD", 4: "ITP_ERR_TIMEOUT",
               5: "ITP_ERR_OOM", 6: "ITP_ERR_STATE", 7: "ITP_ERR_NOCONV"}
@@ -53,6 +54,13 @@ SIGNATURES = [
                               ctypes.POINTER(ctypes.c_double)]),
     ("itp_orthonormalize_noalloc", _I, [ctypes.c_void_p, ctypes.c_void_p, _I, ctypes.c_longlong,
                                         _D, ctypes.c_void_p]),
+    ("itp_create_batch", _I, [ctypes.POINTER(_H), _I, _PD, _PD, _PD, _PD, _I, ctypes.c_void_p]),
+    ("itp_batch_problem", _H, [_H, _I]),
+    ("itp_batch_count", _I, [_H]),
+    ("itp_batch_step", _I, [_H, _I, _D, _I, _PD]),
+    ("itp_batch_kernel_launches", ctypes.c_longlong, [_H]),
+    ("itp_batch_last_error", ctypes.c_char_p, [_H]),
+    ("itp_batch_destroy", None, [_H]),
 ]
 
 KERNEL_KINDS = ["plane_fwd", "plane_merged", "plane_combine", "plane_hpsi", "pencil",
@@ -202,6 +210,48 @@ def itp_orthonormalize_noalloc(phi_device_ptr: int, psi_device_ptr: int, m: int,
         raise ItpError(code, "itp_orthonormalize_noalloc failed")
 
 
+def _check_batch(b, code: int):
+    if code != ITP_OK:
+        msg = load().itp_batch_last_error(b)
+        raise ItpError(code, msg.decode() if msg else "")
+
+
+def itp_create_batch(dims, boxes, n_states, n_guard=None, precision=ITP_MIXED, cuda_stream=0):
+    """dims: (count, 3) ints (nx, ny, nz); boxes: (count, 3) box lengths."""
+    dims = np.ascontiguousarray(dims, dtype=np.int32).reshape(-1, 3)
+    boxes = np.ascontiguousarray(boxes, dtype=np.float64).reshape(-1, 3)
+    ns = np.ascontiguousarray(n_states, dtype=np.int32)
+    count = dims.shape[0]
+    if boxes.shape[0] != count or ns.size != count:
+        raise ValueError("dims, boxes and n_states need one entry per problem")
+    ng = None if n_guard is None else np.ascontiguousarray(n_guard, dtype=np.int32)
+    if ng is not None and ng.size != count:
+        raise ValueError("n_guard needs one entry per problem")
+    b = _H()
+    code = load().itp_create_batch(ctypes.byref(b), count, dims.ctypes.data, boxes.ctypes.data,
+                                   ns.ctypes.data, None if ng is None else ng.ctypes.data,
+                                   precision, ctypes.c_void_p(cuda_stream or None))
+    _check_batch(None, code)
+    return b
+
+
+def itp_batch_problem(b, p: int):
+    h = load().itp_batch_problem(b, int(p))
+    if not h:
+        raise IndexError(f"no problem {p} in the batch")
+    return _H(h)
+
+
+def itp_batch_step(b, order, tau, flags=ITP_RITZ_VALUES, out: np.ndarray | None = None):
+    ptr = None if out is None else out.ctypes.data
+    _check_batch(b, load().itp_batch_step(b, int(order), float(tau), int(flags), ptr))
+    return out
+
+
+def itp_batch_destroy(b):
+    load().itp_batch_destroy(b)
+
+
 # ---- a thin object wrapper -----------------------------------------------------
 class ItpGrid:
     """One problem on the GPU: owns an itp_handle."""
@@ -215,10 +265,23 @@ class ItpGrid:
         self.h = itp_create_grid(nx, ny, nz, lx, ly, lz, n_states, n_guard, precision,
                                  cuda_stream)
 
+    @classmethod
+    def borrowed(cls, h, shape, n_states, n_guard):
+        """Wrap a handle owned elsewhere (a problem of an ItpBatch)."""
+        self = cls.__new__(cls)
+        nz, ny, nx = shape
+        self.shape = (nz, ny, nx)
+        self.n_points = nx * ny * nz
+        self.n_states, self.n_guard = n_states, n_guard
+        self.m = n_states + n_guard
+        self.h = h
+        self._owner = False
+        return self
+
     def close(self):
-        if self.h:
+        if self.h and getattr(self, "_owner", True):
             itp_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __enter__(self):
         return self
@@ -288,3 +351,57 @@ class ItpGrid:
     def profile_read(self):
         """{kind name: (launches, total ms)} since the last profile() call."""
         return {name: itp_profile_read(self.h, k) for k, name in enumerate(KERNEL_KINDS)}
+
+
+class ItpBatch:
+    """Independent problems of uneven size advanced together (one CUDA graph
+    launch per step of all of them); owns an itp_batch_handle."""
+
+    def __init__(self, dims, boxes, n_states, n_guard=None, precision=ITP_MIXED, cuda_stream=0):
+        dims = np.asarray(dims, dtype=np.int64).reshape(-1, 3)
+        ng = np.zeros(len(dims), dtype=np.int64) if n_guard is None else np.asarray(n_guard)
+        self.b = itp_create_batch(dims, boxes, n_states, n_guard, precision, cuda_stream)
+        self.problems = [ItpGrid.borrowed(itp_batch_problem(self.b, p),
+                                          (int(d[2]), int(d[1]), int(d[0])), int(n), int(g))
+                         for p, (d, n, g) in enumerate(zip(dims, n_states, ng))]
+        self.m_total = sum(q.m for q in self.problems)
+
+    def __len__(self):
+        return len(self.problems)
+
+    def __getitem__(self, p):
+        return self.problems[p]
+
+    def step(self, order, tau, ritz=True, fp64=False):
+        """One step of every problem; returns the list of per-problem energies."""
+        flags = (ITP_RITZ_VALUES if ritz else 0) | (ITP_STEP_FP64 if fp64 else 0)
+        out = np.empty(self.m_total, dtype=np.float64)
+        itp_batch_step(self.b, order, tau, flags, out)
+        res, off = [], 0
+        for q in self.problems:
+            res.append(out[off:off + q.m])
+            off += q.m
+        return res
+
+    @property
+    def kernel_launches(self):
+        return int(load().itp_batch_kernel_launches(self.b))
+
+    def close(self):
+        if self.b:
+            for q in self.problems:
+                q.h = None
+            itp_batch_destroy(self.b)
+            self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
