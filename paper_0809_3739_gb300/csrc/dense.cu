@@ -3,9 +3,12 @@
 // symmetric eigen-decomposition, and the application of an n x n matrix to
 // the block of states.  These are the CUDA-core versions; all small-matrix
 // work is FP64.
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include "itp_kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace itp {
 
@@ -108,54 +111,173 @@ __global__ void gram_reduce_kernel(const double* __restrict__ partial, int n_chu
 }
 
 // ---------------------------------------------------------------------------
-// Cholesky (right-looking, column by column) and the lower-triangular
-// inverse by forward substitution, one CTA, matrix in shared memory.
-__global__ void __launch_bounds__(1024) cholesky_inverse_kernel(const double* __restrict__ S,
-                                                                int m, double* __restrict__ Minv,
-                                                                int* status) {
-  extern __shared__ double sh[];
-  const int P = m + 1;
-  double* L = sh;              // m x P
-  __shared__ int bad;
-  if (threadIdx.x == 0) bad = 0;
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    const int i = e / m, j = e - i * m;
-    L[i * P + j] = S[e];
+// Cholesky S = L L^T and M = L^{-1} (right-looking, column by column) on a
+// cluster of kClus CTAs, for the FP64 rate: an SM retires about two FP64 FMAs per clock, so the O(m^3) work is spread
+// over the cluster's SMs.  CTA r owns rows [r*rp, r*rp + rp) of S (lower
+// part) and of R = I - sum_j L[:, j] M[j, :], in its shared memory; other
+// CTAs read them through distributed shared memory.  Step k (one cluster
+// barrier): every CTA reads the pivot S[k][k], column k of the updated S
+// (giving column k of L) and row k of R (giving row k of M = L^{-1}), then
+// updates its own rows i > k:
+//   S[i][j] -= L[i][k] L[j][k]  (k < j <= i),   R[i][j] -= L[i][k] M[k][j]  (j <= k).
+// Nothing a step reads remotely (column k of S, row k of R) is written in
+// that step, so one barrier per step orders everything.
+constexpr int kClus = 8;                      // CTAs per cluster (portable size)
+constexpr int kClusRows = kMaxM / kClus;      // rows per CTA at most
+constexpr int kClusThreads = 256;
+constexpr int kClusPitch = kMaxM + 1;
+
+__global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kClusThreads)
+    cholesky_inverse_cluster_kernel(const double* __restrict__ S, int m,
+                                    double* __restrict__ Minv, int* status) {
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ double A[kClusRows][kClusPitch];
+  __shared__ double Rr[kClusRows][kClusPitch];
+  __shared__ double lf[kMaxM], mk[kMaxM];
+  __shared__ double s_piv;
+  __shared__ int s_bad;
+  const int rank = (int)cl.block_rank();
+  const int rp = (m + kClus - 1) / kClus;
+  const int r0 = rank * rp, r1 = max(r0, min(m, r0 + rp));
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = kClusThreads / 32;
+  if (tid == 0) s_bad = 0;
+  for (int q = tid; q < (r1 - r0) * m; q += kClusThreads) {
+    const int il = q / m, j = q - il * m;
+    A[il][j] = S[(long long)(r0 + il) * m + j];
+    Rr[il][j] = (r0 + il == j) ? 1.0 : 0.0;
   }
-  __syncthreads();
+  cl.sync();
   for (int k = 0; k < m; ++k) {
-    if (threadIdx.x == 0) {
-      const double d = L[k * P + k];
-      if (!(d > 0.0) || !isfinite(d)) {
-        bad = 1;
-        L[k * P + k] = 1.0;
-      } else {
-        L[k * P + k] = sqrt(d);
+    const int ok = k / rp;
+    if (tid == 0) {
+      const double akk = *cl.map_shared_rank(&A[k - ok * rp][k], ok);
+      double piv = 1.0;
+      if (!(akk > 0.0) || !isfinite(akk)) s_bad = 1;
+      else piv = sqrt(akk);
+      s_piv = piv;
+    }
+    __syncthreads();
+    const double rpiv = 1.0 / s_piv;
+    for (int j = k + 1 + tid; j < m; j += kClusThreads) {
+      const int o = j / rp;
+      lf[j] = *cl.map_shared_rank(&A[j - o * rp][k], o) * rpiv;
+    }
+    for (int j = tid; j <= k; j += kClusThreads)
+      mk[j] = *cl.map_shared_rank(&Rr[k - ok * rp][j], ok) * rpiv;
+    __syncthreads();
+    if (rank == ok)
+      for (int j = tid; j < m; j += kClusThreads) Minv[(long long)k * m + j] = j <= k ? mk[j] : 0.0;
+    // own rows i > k: one warp per row, lanes over columns
+    for (int i = max(r0, k + 1) + warp; i < r1; i += NW) {
+      const int il = i - r0;
+      const double li = lf[i];
+      for (int j = lane; j <= i; j += 32) {
+        if (j <= k) Rr[il][j] -= li * mk[j];
+        else A[il][j] -= li * lf[j];
       }
     }
+    cl.sync();
+  }
+  if (tid == 0 && s_bad) atomicOr(status, 1);
+}
+
+// Householder tridiagonalisation (eigenvalues only) on a cluster: CTA r
+// owns full rows [r*rp, r*rp + rp) of the symmetric matrix.  Step k takes
+// two cluster barriers: after the partial sums of squares of column k
+// (giving the reflector, which every CTA forms alike from the same values in
+// the same order), and after the partial products p = beta A v and v^T p;
+// then each CTA applies A -= v w^T + w v^T to its own rows.
+__global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kClusThreads)
+    tridiag_cluster_kernel(const double* __restrict__ H, int m, double* __restrict__ d,
+                           double* __restrict__ e) {
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ double A[kClusRows][kClusPitch];
+  __shared__ double vf[kMaxM], wf[kMaxM];
+  __shared__ double pl[kClusRows];       // own entries of p (read by the others)
+  __shared__ double s_sig[2], s_dot[2];  // partial sums (read by the others)
+  __shared__ double s_beta, s_K;
+  const int rank = (int)cl.block_rank();
+  const int rp = (m + kClus - 1) / kClus;
+  const int r0 = rank * rp, r1 = max(r0, min(m, r0 + rp));
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = kClusThreads / 32;
+  for (int q = tid; q < (r1 - r0) * m; q += kClusThreads) {
+    const int il = q / m, j = q - il * m, i = r0 + il;
+    A[il][j] = 0.5 * (H[(long long)i * m + j] + H[(long long)j * m + i]);
+  }
+  __syncthreads();
+  for (int k = 0; k + 2 < m; ++k) {
+    const int n0 = k + 1, b = k & 1;
+    if (warp == 0) {
+      double sig = 0.0;
+      for (int i = max(r0, n0 + 1) + lane; i < r1; i += 32) sig += A[i - r0][k] * A[i - r0][k];
+      for (int o = 16; o; o >>= 1) sig += __shfl_xor_sync(0xffffffffu, sig, o);
+      if (lane == 0) s_sig[b] = sig;
+    }
+    if (tid == 0 && k >= r0 && k < r1) d[k] = A[k - r0][k];
+    cl.sync();
+    if (tid == 0) {
+      double sig = 0.0;
+      for (int r = 0; r < kClus; ++r) sig += *cl.map_shared_rank(&s_sig[b], r);
+      const int o = n0 / rp;
+      const double x0 = *cl.map_shared_rank(&A[n0 - o * rp][k], o);
+      double alpha = x0, beta = 0.0, v0 = 0.0;
+      if (sig != 0.0) {
+        const double nrm = sqrt(x0 * x0 + sig);
+        alpha = x0 > 0 ? -nrm : nrm;
+        v0 = x0 - alpha;
+        beta = 2.0 / (v0 * v0 + sig);
+      }
+      s_beta = beta;
+      vf[n0] = v0;
+      if (rank == 0) e[k] = alpha;
+    }
+    for (int j = n0 + 1 + tid; j < m; j += kClusThreads) {
+      const int o = j / rp;
+      vf[j] = *cl.map_shared_rank(&A[j - o * rp][k], o);
+    }
     __syncthreads();
-    const double piv = L[k * P + k];
-    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) L[i * P + k] /= piv;
+    const double beta = s_beta;
+    for (int i = max(r0, n0) + warp; i < r1; i += NW) {
+      double acc = 0.0;
+      for (int j = n0 + lane; j < m; j += 32) acc += A[i - r0][j] * vf[j];
+      for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) pl[i - r0] = beta * acc;
+    }
     __syncthreads();
-    const int rem = m - k - 1;
-    for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
-      const int i = k + 1 + e / rem, j = k + 1 + e % rem;
-      if (j <= i) L[i * P + j] -= L[i * P + k] * L[j * P + k];
+    if (warp == 0) {
+      double acc = 0.0;
+      for (int i = max(r0, n0) + lane; i < r1; i += 32) acc += vf[i] * pl[i - r0];
+      for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) s_dot[b] = acc;
+    }
+    cl.sync();
+    if (tid == 0) {
+      double dot = 0.0;
+      for (int r = 0; r < kClus; ++r) dot += *cl.map_shared_rank(&s_dot[b], r);
+      s_K = 0.5 * beta * dot;
+    }
+    __syncthreads();
+    const double K = s_K;
+    for (int j = n0 + tid; j < m; j += kClusThreads) {
+      const int o = j / rp;
+      wf[j] = *cl.map_shared_rank(&pl[j - o * rp], o) - K * vf[j];
+    }
+    __syncthreads();
+    for (int i = max(r0, n0) + warp; i < r1; i += NW) {
+      const int il = i - r0;
+      const double vi = vf[i], wi = wf[i];
+      for (int j = n0 + lane; j < m; j += 32) A[il][j] -= vi * wf[j] + wi * vf[j];
     }
     __syncthreads();
   }
-  // Minv = L^{-1}: column j solves L x = e_j by forward substitution; each
-  // thread owns one column of the output in global memory.
-  for (int j = threadIdx.x; j < m; j += blockDim.x) {
-    for (int i = 0; i < j; ++i) Minv[i * m + j] = 0.0;
-    Minv[j * m + j] = 1.0 / L[j * P + j];
-    for (int i = j + 1; i < m; ++i) {
-      double s = 0.0;
-      for (int k = j; k < i; ++k) s = fma(L[i * P + k], Minv[k * m + j], s);
-      Minv[i * m + j] = -s / L[i * P + i];
-    }
+  if (tid == 0) {
+    if (m >= 2 && m - 2 >= r0 && m - 2 < r1) d[m - 2] = A[m - 2 - r0][m - 2];
+    if (m >= 2 && m - 1 >= r0 && m - 1 < r1) e[m - 2] = A[m - 1 - r0][m - 2];
+    if (m - 1 >= r0 && m - 1 < r1) d[m - 1] = A[m - 1 - r0][m - 1];
   }
-  if (threadIdx.x == 0 && bad) atomicOr(status, 1);
+  cl.sync();   // no CTA leaves while another may still read its shared memory
 }
 
 // ---------------------------------------------------------------------------
@@ -269,93 +391,10 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const double* __restrict__
 }
 
 // ---------------------------------------------------------------------------
-// Eigenvalues only: Householder reduction of the symmetric m x m matrix to
-// tridiagonal form (one CTA, matrix in shared memory), then bisection on
-// Sturm counts with one warp per eigenvalue (32-point multisection), spread
-// over many SMs because each SM's FP64 pipe is narrow.
-__global__ void __launch_bounds__(1024) tridiag_kernel(const double* __restrict__ H, int m,
-                                                       double* __restrict__ d,
-                                                       double* __restrict__ e) {
-  extern __shared__ double sh[];
-  const int P = m + 1;
-  double* A = sh;               // m x P
-  double* v = A + m * P;        // [m]
-  double* p = v + m;            // [m]
-  __shared__ double s_alpha, s_beta, s_K;
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
-  for (int q = tid; q < m * m; q += nthr) {
-    const int i = q / m, j = q - i * m;
-    A[i * P + j] = 0.5 * (H[i * m + j] + H[j * m + i]);
-  }
-  __syncthreads();
-  for (int k = 0; k + 2 < m; ++k) {
-    const int n0 = k + 1, nk = m - n0;
-    // Householder vector of x = A[n0.., k]
-    if (warp == 0) {
-      double sig = 0.0;
-      for (int i = n0 + 1 + lane; i < m; i += 32) sig += A[i * P + k] * A[i * P + k];
-      for (int o = 16; o; o >>= 1) sig += __shfl_xor_sync(0xffffffffu, sig, o);
-      if (lane == 0) {
-        const double x0 = A[n0 * P + k];
-        if (sig == 0.0) {
-          s_alpha = x0;
-          s_beta = 0.0;
-        } else {
-          const double nrm = sqrt(x0 * x0 + sig);
-          const double alpha = x0 > 0 ? -nrm : nrm;
-          const double v0 = x0 - alpha;
-          s_alpha = alpha;
-          s_beta = 2.0 / (v0 * v0 + sig);
-          v[n0] = v0;
-        }
-      }
-    }
-    __syncthreads();
-    const double beta = s_beta;
-    if (tid == 0) {
-      d[k] = A[k * P + k];
-      e[k] = s_alpha;
-    }
-    if (beta == 0.0) {   // already tridiagonal in this column
-      __syncthreads();
-      continue;
-    }
-    for (int i = n0 + 1 + tid; i < m; i += nthr) v[i] = A[i * P + k];
-    __syncthreads();
-    // p = beta * A_sub v   (one warp per row)
-    for (int i = n0 + warp; i < m; i += nw) {
-      double acc = 0.0;
-      for (int j = n0 + lane; j < m; j += 32) acc += A[i * P + j] * v[j];
-      for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) p[i] = beta * acc;
-    }
-    __syncthreads();
-    if (warp == 0) {
-      double acc = 0.0;
-      for (int i = n0 + lane; i < m; i += 32) acc += v[i] * p[i];
-      for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) s_K = 0.5 * beta * acc;
-    }
-    __syncthreads();
-    const double K = s_K;
-    for (int i = n0 + tid; i < m; i += nthr) p[i] -= K * v[i];   // p becomes w
-    __syncthreads();
-    for (int q = tid; q < nk * nk; q += nthr) {
-      const int i = n0 + q / nk, j = n0 + q % nk;
-      A[i * P + j] -= v[i] * p[j] + p[i] * v[j];
-    }
-    __syncthreads();
-  }
-  if (tid == 0) {
-    if (m >= 2) {
-      d[m - 2] = A[(m - 2) * P + (m - 2)];
-      e[m - 2] = A[(m - 1) * P + (m - 2)];
-    }
-    d[m - 1] = A[(m - 1) * P + (m - 1)];
-  }
-}
-
+// Eigenvalues only: the cluster tridiagonalisation above, then bisection on
+// Sturm counts with one warp per eigenvalue (32-point multisection), one
+// warp per CTA so that the FP64 work spreads over as many SMs as there are
+// eigenvalues.
 // Number of eigenvalues of the tridiagonal (d, e) below x (Sturm count of
 // the LDL^T pivots, with the usual guard against a zero pivot).
 __device__ __forceinline__ int sturm_count(const double* d, const double* e2, int m, double x,
@@ -374,7 +413,7 @@ __device__ __forceinline__ int sturm_count(const double* d, const double* e2, in
 
 // One warp per eigenvalue index j: 32-point multisection of a bracket of
 // the j-th smallest eigenvalue down to a few ulps.
-__global__ void __launch_bounds__(128) bisect_kernel(const double* __restrict__ dg,
+__global__ void __launch_bounds__(32) bisect_kernel(const double* __restrict__ dg,
                                                      const double* __restrict__ eg, int m,
                                                      double* __restrict__ E) {
   __shared__ double sd[kMaxM], se2[kMaxM];
@@ -506,12 +545,8 @@ cudaError_t launch_gram_reduce(const double* partial, int n_chunks, int m, doubl
 
 cudaError_t launch_cholesky_inverse(const double* S, int m, double* Minv, int* status,
                                     cudaStream_t st) {
-  if (m > kMaxM) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)m * (m + 1) * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(cholesky_inverse_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  cholesky_inverse_kernel<<<1, 1024, smem, st>>>(S, m, Minv, status);
+  if (m < 1 || m > kMaxM) return cudaErrorInvalidValue;
+  cholesky_inverse_cluster_kernel<<<kClus, kClusThreads, 0, st>>>(S, m, Minv, status);
   return cudaGetLastError();
 }
 
@@ -529,18 +564,14 @@ cudaError_t launch_jacobi_eigh(const double* H, int m, double* E, double* Rt, do
 }
 
 cudaError_t launch_tridiag(const double* H, int m, double* work, cudaStream_t st) {
-  if (m > kMaxM) return cudaErrorInvalidValue;
-  const size_t smem = ((size_t)m * (m + 1) + 2 * (size_t)m) * sizeof(double);
-  cudaError_t err = cudaFuncSetAttribute(tridiag_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
-  tridiag_kernel<<<1, 1024, smem, st>>>(H, m, work, work + m);
+  if (m < 1 || m > kMaxM) return cudaErrorInvalidValue;
+  tridiag_cluster_kernel<<<kClus, kClusThreads, 0, st>>>(H, m, work, work + m);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bisect(const double* work, int m, double* E, cudaStream_t st) {
   if (m > kMaxM) return cudaErrorInvalidValue;
-  bisect_kernel<<<(m + 3) / 4, 128, 0, st>>>(work, work + m, m, E);
+  bisect_kernel<<<m, 32, 0, st>>>(work, work + m, m, E);
   return cudaGetLastError();
 }
 
