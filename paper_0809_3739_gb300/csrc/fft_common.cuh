@@ -33,6 +33,25 @@ template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
 template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
   C r; r.x = a.x * b.x + a.y * b.y; r.y = a.y * b.x - a.x * b.y; return r;
 }
+// FP32 complex values use the packed two-lane FP32 instructions of sm_100+
+// (one instruction updates re and im): add, multiply and fused multiply-add
+// on float2.  Each lane rounds as the scalar instruction does.
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) {
+  return __fadd2_rn(a, b);
+}
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+  return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
+template <> __device__ __forceinline__ float2 cmul<float2>(float2 a, float2 b) {
+  // (a.x b.x, a.x b.y) + (a.y (-b.y), a.y b.x)
+  return __ffma2_rn(make_float2(a.y, a.y), make_float2(-b.y, b.x),
+                    __fmul2_rn(make_float2(a.x, a.x), b));
+}
+template <> __device__ __forceinline__ float2 cmulc<float2>(float2 a, float2 b) {
+  // (a.x b.x, -a.x b.y) + (a.y b.y, a.y b.x)
+  return __ffma2_rn(make_float2(a.y, a.y), make_float2(b.y, b.x),
+                    __fmul2_rn(make_float2(a.x, a.x), make_float2(b.x, -b.y)));
+}
 // multiply by i*s, s = +-1
 template <int S, typename C> __device__ __forceinline__ C cmul_i(C a) {
   C r; if (S > 0) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; } return r;

@@ -133,6 +133,10 @@ __device__ __forceinline__ C cmulri(C a, C f) {  // (a.x * f.x, a.y * f.y)
   a.y *= f.y;
   return a;
 }
+template <>
+__device__ __forceinline__ float2 cmulri<float2>(float2 a, float2 f) {
+  return __fmul2_rn(a, f);
+}
 
 // ----------------------------------------------------------------------------
 // Shared-memory geometry of one plane.
