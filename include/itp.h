@@ -183,6 +183,47 @@ int itp_profile(itp_handle h, int enable);
  * the last itp_profile call.  Synchronises. */
 int itp_profile_read(itp_handle h, int kind, long long* launches, double* total_ms);
 
+/* ---- Launch shapes and the autotuner ----------------------------------------
+ * The paper fixes the arithmetic, not how it is cut into GPU work.  A handle
+ * carries four launch-shape choices for its main precision lane (FP32 for
+ * ITP_MIXED, FP64 for ITP_FP64), as an int[ITP_TUNING_LEN]:
+ *   [ITP_TUNE_PENCIL_W]  kx columns per pencil-pass CTA, 1..nx/2+1 (and the
+ *                        FP64 pencil slab, nz*(w+1) complex doubles, within
+ *                        one CTA's 227 KB of shared memory)
+ *   [ITP_TUNE_SPLIT]     0: one CTA per plane for the x and y transforms
+ *                        (only where the plane fits one CTA); 1: row passes
+ *                        (x) and column passes (y)
+ *   [ITP_TUNE_ROW_TB]    row pairs per row-pass CTA with ITP_TUNE_SPLIT = 1:
+ *                        8, 16, or 32 (32: FP32 with nx = 256 only); it
+ *                        divides ny/2
+ *   [ITP_TUNE_GRAM]      CTAs (partial sums) of the overlap kernel,
+ *                        1..2 x the SM count
+ * Results depend on the shapes only through rounding. */
+#define ITP_TUNE_PENCIL_W 0
+#define ITP_TUNE_SPLIT 1
+#define ITP_TUNE_ROW_TB 2
+#define ITP_TUNE_GRAM 3
+#define ITP_TUNING_LEN 4
+
+/* Current launch shapes of the handle's main lane. */
+int itp_get_tuning(itp_handle h, int* tuning);
+
+/* Set the launch shapes (all four); ITP_ERR_ARG if one is not valid for the
+ * grid (the handle keeps its previous shapes).  Later steps use them;
+ * itp_step recaptures its graph. */
+int itp_set_tuning(itp_handle h, const int* tuning);
+
+/* Time the candidate shapes on the handle's own potential and states and
+ * keep the fastest: the plane-pass form and the pencil width by timing
+ * itp_propagate(order, tau), then the overlap's CTA count by timing its
+ * kernel.  The states are not changed (the timed propagations write only
+ * the propagated block, which is discarded).  tuning (nullable) receives
+ * the chosen shapes, report (nullable) a one-line summary of the candidates
+ * and their times (truncated to report_len bytes, NUL-terminated).
+ * Synchronises. */
+int itp_autotune(itp_handle h, int order, double tau, int* tuning, char* report,
+                 int report_len);
+
 /* ---- Batches of independent problems ----------------------------------------
  * Many independent problems of uneven size -- each with its own grid,
  * potential and state count -- advanced together.  The paper treats one

@@ -2,6 +2,7 @@
 Krotscheck): a CUDA library with a C ABI (include/itp.h, libitp.so) and its
 ctypes binding."""
 from .itp import (ITP_FP64, ITP_MIXED, ITP_RITZ, ITP_RITZ_VALUES, ITP_STEP_FP64,  # noqa: F401
+                  itp_autotune, itp_get_tuning, itp_set_tuning,
                   ItpBatch, ItpError, ItpGrid, itp_batch_destroy, itp_batch_problem,
                   itp_batch_step, itp_create_batch, itp_create_grid, itp_destroy,
                   itp_energies, itp_get_phi, itp_get_states, itp_kernel_launches,

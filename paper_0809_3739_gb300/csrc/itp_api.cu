@@ -3,6 +3,7 @@
 // up one imaginary-time iteration (Eqs. 3 and 4 of the paper).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -74,10 +75,11 @@ struct itp_grid {
   bool own_stream = false;    // created by the library (no stream given)
   // CUDA graph of one step (itp_step): propagate + orthonormalize + energies
   cudaGraphExec_t step_exec = nullptr;
-  int step_order = 0, step_flags = -1, step_lane = -1;
+  int step_order = 0, step_flags = -1, step_lane = -1, step_version = 0;
   double step_tau = 0.0;
   bool capturing = false;
   long long step_launches = 0;
+  int tune_version = 0;       // bumped when the launch shapes change
   // optional per-kernel event timing (itp_profile)
   bool prof = false;
   struct ProfEvent { int kind; cudaEvent_t start, stop; };
@@ -580,6 +582,170 @@ int step_resources(itp_handle h, int k, double tau) {
   return ITP_OK;
 }
 
+// ---- launch shapes --------------------------------------------------------------
+// Index of the handle's main lane in the per-precision shape arrays.
+int main_lane(itp_handle h) { return h->precision == ITP_MIXED ? 0 : 1; }
+
+void get_tuning(itp_handle h, int* t) {
+  const int pi = main_lane(h);
+  t[ITP_TUNE_PENCIL_W] = h->g.pencil_w;
+  t[ITP_TUNE_SPLIT] = h->g.split_planes[pi];
+  t[ITP_TUNE_ROW_TB] = h->g.row_tb[pi];
+  t[ITP_TUNE_GRAM] = pi == 0 ? h->n_chunks_tc : h->n_chunks;
+}
+
+// Validate and apply; returns ITP_OK or ITP_ERR_ARG with a message.
+int set_tuning(itp_handle h, const int* t) {
+  GridDesc& g = h->g;
+  const int pi = main_lane(h);
+  const int rb = pi == 0 ? 4 : 8;
+  const int w = t[ITP_TUNE_PENCIL_W], split = t[ITP_TUNE_SPLIT], tb = t[ITP_TUNE_ROW_TB],
+            chunks = t[ITP_TUNE_GRAM];
+  if (w < 1 || w > g.nxh || ((size_t)g.nz * w + g.nz) * 16 > kSmemLimit)
+    return fail(h, ITP_ERR_ARG, "pencil width %d not in 1..%d or too large", w, g.nxh);
+  if (split != 0 && split != 1) return fail(h, ITP_ERR_ARG, "split must be 0 or 1");
+  if (!split && plane_smem_bytes(g, rb) > kSmemLimit)
+    return fail(h, ITP_ERR_ARG, "a %dx%d plane does not fit one CTA", g.nx, g.ny);
+  if (split && !(tb == 8 || tb == 16 || tb == 32) )
+    return fail(h, ITP_ERR_ARG, "row-pass block %d not 8, 16 or 32", tb);
+  if (split && ((g.ny / 2) % tb != 0 || ((size_t)tb * g.pp + g.nx) * 2 * rb > 96 * 1024 ||
+                (tb == 32 && !(pi == 0 && g.nx == 256))))
+    return fail(h, ITP_ERR_ARG, "row-pass block %d does not suit a %dx%d plane", tb, g.nx, g.ny);
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (chunks < 1 || chunks > 2 * sms)
+    return fail(h, ITP_ERR_ARG, "Gram CTA count %d not in 1..%d", chunks, 2 * sms);
+  g.pencil_w = w;
+  g.pencil_pitch = w;
+  g.split_planes[pi] = split;
+  g.row_tb[pi] = split ? tb : 0;
+  if (split) {
+    const size_t budget = 72 * 1024, full = (size_t)g.ny * g.nxh * 2 * rb;
+    const int c = (int)((full + budget - 1) / budget);
+    g.col_w[pi] = (g.nxh + c - 1) / c;
+  }
+  if (pi == 0) h->n_chunks_tc = chunks;
+  else h->n_chunks = chunks;
+  h->tune_version++;
+  return ITP_OK;
+}
+
+// Device time (ms) of `reps` calls of fn after one untimed call.
+template <typename F>
+int time_ms(itp_handle h, int reps, float* ms, F&& fn) {
+  ITP_TRY(fn());
+  cudaEvent_t a = nullptr, b = nullptr;
+  ITP_CUDA(h, cudaEventCreate(&a));
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return fail(h, ITP_ERR_CUDA, "event");
+  }
+  int rc = ITP_OK;
+  cudaEventRecord(a, h->st);
+  for (int r = 0; r < reps && rc == ITP_OK; ++r) rc = fn();
+  cudaEventRecord(b, h->st);
+  if (rc == ITP_OK && cudaEventSynchronize(b) != cudaSuccess)
+    rc = fail(h, ITP_ERR_CUDA, "timing");
+  float t = 0.f;
+  if (rc == ITP_OK) cudaEventElapsedTime(&t, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *ms = t / reps;
+  return rc;
+}
+
+template <typename R>
+int autotune_lane(itp_handle h, int k, double tau, std::string& rep) {
+  ITP_TRY(step_resources<R>(h, k, tau));
+  const GridDesc& g = h->g;
+  const int pi = main_lane(h);
+  const int rb = pi == 0 ? 4 : 8;
+  int best[ITP_TUNING_LEN], cur[ITP_TUNING_LEN];
+  get_tuning(h, best);
+  char buf[96];
+  auto prop = [&]() { return propagate_lane<R>(h, k, tau); };
+  // 1. plane-pass form: whole planes (where they fit) or row + column passes
+  {
+    std::vector<std::pair<int, int>> forms;   // (split, tb)
+    if (plane_smem_bytes(g, rb) <= kSmemLimit) forms.push_back({0, 0});
+    for (int tb : {32, 16, 8})
+      if ((g.ny / 2) % tb == 0 && ((size_t)tb * g.pp + g.nx) * 2 * rb <= 96 * 1024 &&
+          (tb != 32 || (pi == 0 && g.nx == 256)))
+        forms.push_back({1, tb});
+    float best_ms = 1e30f;
+    rep += "planes:";
+    for (auto [split, tb] : forms) {
+      memcpy(cur, best, sizeof(cur));
+      cur[ITP_TUNE_SPLIT] = split;
+      cur[ITP_TUNE_ROW_TB] = tb;
+      if (set_tuning(h, cur) != ITP_OK) continue;
+      float ms = 0.f;
+      ITP_TRY(time_ms(h, 2, &ms, prop));
+      snprintf(buf, sizeof(buf), " %s=%.3fms", split ? ("split" + std::to_string(tb)).c_str()
+                                                     : "whole", ms);
+      rep += buf;
+      if (ms < best_ms) {
+        best_ms = ms;
+        memcpy(best, cur, sizeof(cur));
+      }
+    }
+    ITP_TRY(set_tuning(h, best));
+  }
+  // 2. pencil width: nx/2+1 columns cut into 1..4 blocks
+  {
+    float best_ms = 1e30f;
+    int last = -1;
+    rep += "; pencil_w:";
+    for (int c = 1; c <= 4; ++c) {
+      const int w = (g.nxh + c - 1) / c;
+      if (w == last) continue;
+      last = w;
+      memcpy(cur, best, sizeof(cur));
+      cur[ITP_TUNE_PENCIL_W] = w;
+      if (set_tuning(h, cur) != ITP_OK) continue;
+      float ms = 0.f;
+      ITP_TRY(time_ms(h, 2, &ms, prop));
+      snprintf(buf, sizeof(buf), " %d=%.3fms", w, ms);
+      rep += buf;
+      if (ms < best_ms) {
+        best_ms = ms;
+        memcpy(best, cur, sizeof(cur));
+      }
+    }
+    ITP_TRY(set_tuning(h, best));
+  }
+  // 3. CTAs of the overlap kernel, timed on the propagated block
+  {
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    float best_ms = 1e30f;
+    rep += "; gram:";
+    for (int chunks : {sms, 2 * sms}) {
+      float ms = 0.f;
+      auto gram = [&]() -> int {
+        cudaError_t e;
+        if (pi == 0)
+          e = launch_tc_gram(h->f32.psi_tmp, h->f32.psi_tmp, h->m, g.n_points, chunks,
+                             h->partial, h->status, h->st);
+        else
+          e = launch_gram_partial<double, double, double>(h->acc, h->acc, h->m, g.n_points,
+                                                          chunks, h->partial, h->st);
+        return e == cudaSuccess ? ITP_OK : fail(h, ITP_ERR_CUDA, "gram: %s",
+                                                cudaGetErrorString(e));
+      };
+      ITP_TRY(time_ms(h, 3, &ms, gram));
+      snprintf(buf, sizeof(buf), " %d=%.3fms", chunks, ms);
+      rep += buf;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best[ITP_TUNE_GRAM] = chunks;
+      }
+    }
+    ITP_TRY(set_tuning(h, best));
+  }
+  return ITP_OK;
+}
+
 }  // namespace
 
 // A batch of independent problems: one handle (and stream) per problem and
@@ -596,6 +762,7 @@ struct itp_batch {
   cudaGraphExec_t exec = nullptr;
   int order = 0, flags = -1;
   double tau = 0.0;
+  std::vector<int> versions;   // problems' launch-shape versions at capture
   long long step_launches = 0, launches = 0;
   std::string err;
 };
@@ -921,7 +1088,7 @@ int itp_step(itp_handle h, int order, double tau, int flags, double* E_host) {
     lane = 1;
   }
   if (!h->step_exec || h->step_order != order || h->step_tau != tau ||
-      h->step_flags != flags || h->step_lane != lane) {
+      h->step_flags != flags || h->step_lane != lane || h->step_version != h->tune_version) {
     if (h->step_exec) {
       cudaGraphExecDestroy(h->step_exec);
       h->step_exec = nullptr;
@@ -949,6 +1116,7 @@ int itp_step(itp_handle h, int order, double tau, int flags, double* E_host) {
     h->step_tau = tau;
     h->step_flags = flags;
     h->step_lane = lane;
+    h->step_version = h->tune_version;
   }
   ITP_CUDA(h, cudaGraphLaunch(h->step_exec, h->st));
   h->launches += h->step_launches;
@@ -1034,6 +1202,53 @@ int itp_profile_read(itp_handle h, int kind, long long* launches, double* total_
   }
   if (launches) *launches = n;
   if (total_ms) *total_ms = ms;
+  return ITP_OK;
+}
+
+int itp_get_tuning(itp_handle h, int* tuning) {
+  if (!h || !tuning) return h ? fail(h, ITP_ERR_ARG, "null tuning") : ITP_ERR_ARG;
+  get_tuning(h, tuning);
+  return ITP_OK;
+}
+
+int itp_set_tuning(itp_handle h, const int* tuning) {
+  if (!h || !tuning) return h ? fail(h, ITP_ERR_ARG, "null tuning") : ITP_ERR_ARG;
+  ITP_CUDA(h, cudaSetDevice(h->device));
+  ITP_CUDA(h, cudaStreamSynchronize(h->st));
+  int old[ITP_TUNING_LEN];
+  get_tuning(h, old);
+  const int rc = set_tuning(h, tuning);
+  if (rc != ITP_OK) set_tuning(h, old);
+  return rc;
+}
+
+int itp_autotune(itp_handle h, int order, double tau, int* tuning, char* report,
+                 int report_len) {
+  ITP_TRY(check_ready(h, true));
+  if (order < 2 || order > 2 * kMaxTerms || (order & 1))
+    return fail(h, ITP_ERR_ARG, "order must be even, 2..%d (got %d)", 2 * kMaxTerms, order);
+  if (!(tau > 0) || !std::isfinite(tau)) return fail(h, ITP_ERR_ARG, "tau must be > 0");
+  ITP_CUDA(h, cudaStreamSynchronize(h->st));
+  const bool had_phi = h->have_phi;
+  std::string rep;
+  int rc;
+  if (h->precision == ITP_MIXED) {
+    ITP_TRY(switch_lane<float>(h));
+    rc = autotune_lane<float>(h, order / 2, tau, rep);
+  } else {
+    rc = autotune_lane<double>(h, order / 2, tau, rep);
+  }
+  // the timed propagations overwrote the propagated block
+  h->have_phi = false;
+  (void)had_phi;
+  if (rc != ITP_OK) return rc;
+  ITP_CUDA(h, cudaStreamSynchronize(h->st));
+  if (tuning) get_tuning(h, tuning);
+  if (report && report_len > 0) {
+    const size_t n = std::min(rep.size(), (size_t)report_len - 1);
+    memcpy(report, rep.data(), n);
+    report[n] = 0;
+  }
   return ITP_OK;
 }
 
@@ -1134,7 +1349,9 @@ int itp_batch_step(itp_batch_handle b, int order, double tau, int flags, double*
         cudaStreamWaitEvent(b->st, b->join[p], 0) != cudaSuccess)
       return batch_fail(b, ITP_ERR_CUDA, "stream ordering");
   }
-  if (!b->exec || b->order != order || b->tau != tau || b->flags != flags) {
+  bool stale = (int)b->versions.size() != np;
+  for (int p = 0; p < np && !stale; ++p) stale = b->versions[p] != b->probs[p]->tune_version;
+  if (!b->exec || stale || b->order != order || b->tau != tau || b->flags != flags) {
     if (b->exec) {
       cudaGraphExecDestroy(b->exec);
       b->exec = nullptr;
@@ -1183,6 +1400,8 @@ int itp_batch_step(itp_batch_handle b, int order, double tau, int flags, double*
     b->tau = tau;
     b->flags = flags;
     b->step_launches = n;
+    b->versions.resize(np);
+    for (int p = 0; p < np; ++p) b->versions[p] = b->probs[p]->tune_version;
   }
   if (cudaGraphLaunch(b->exec, b->st) != cudaSuccess)
     return batch_fail(b, ITP_ERR_CUDA, "graph launch");

@@ -22,6 +22,8 @@ ITP_MIXED = 1
 ITP_RITZ = 1
 ITP_RITZ_VALUES = 2
 ITP_STEP_FP64 = 4
+ITP_TUNE_PENCIL_W, ITP_TUNE_SPLIT, ITP_TUNE_ROW_TB, ITP_TUNE_GRAM = 0, 1, 2, 3
+ITP_TUNING_LEN = 4
 
 _ERR_NAMES = {1: "ITP_ERR_ARG", 2: "ITP_ERR_CUDA", 3: "ITP_ERR_NOT_PD", 4: "ITP_ERR_TIMEOUT",
               5: "ITP_ERR_OOM", 6: "ITP_ERR_STATE", 7: "ITP_ERR_NOCONV"}
@@ -54,6 +56,9 @@ SIGNATURES = [
                               ctypes.POINTER(ctypes.c_double)]),
     ("itp_orthonormalize_noalloc", _I, [ctypes.c_void_p, ctypes.c_void_p, _I, ctypes.c_longlong,
                                         _D, ctypes.c_void_p]),
+    ("itp_get_tuning", _I, [_H, _PD]),
+    ("itp_set_tuning", _I, [_H, _PD]),
+    ("itp_autotune", _I, [_H, _I, _D, _PD, ctypes.c_char_p, _I]),
     ("itp_create_batch", _I, [ctypes.POINTER(_H), _I, _PD, _PD, _PD, _PD, _I, ctypes.c_void_p]),
     ("itp_batch_problem", _H, [_H, _I]),
     ("itp_batch_count", _I, [_H]),
@@ -210,6 +215,26 @@ def itp_orthonormalize_noalloc(phi_device_ptr: int, psi_device_ptr: int, m: int,
         raise ItpError(code, "itp_orthonormalize_noalloc failed")
 
 
+def itp_get_tuning(h) -> dict:
+    t = (ctypes.c_int * ITP_TUNING_LEN)()
+    _check(h, load().itp_get_tuning(h, t))
+    return {"pencil_w": t[0], "split": t[1], "row_tb": t[2], "gram_ctas": t[3]}
+
+
+def itp_set_tuning(h, pencil_w, split, row_tb, gram_ctas):
+    t = (ctypes.c_int * ITP_TUNING_LEN)(int(pencil_w), int(split), int(row_tb), int(gram_ctas))
+    _check(h, load().itp_set_tuning(h, t))
+
+
+def itp_autotune(h, order, tau):
+    """Returns (chosen shapes as a dict, the candidates' timing report)."""
+    t = (ctypes.c_int * ITP_TUNING_LEN)()
+    rep = ctypes.create_string_buffer(1024)
+    _check(h, load().itp_autotune(h, int(order), float(tau), t, rep, len(rep)))
+    return ({"pencil_w": t[0], "split": t[1], "row_tb": t[2], "gram_ctas": t[3]},
+            rep.value.decode())
+
+
 def _check_batch(b, code: int):
     if code != ITP_OK:
         msg = load().itp_batch_last_error(b)
@@ -340,6 +365,15 @@ class ItpGrid:
 
     def synchronize(self):
         itp_synchronize(self.h)
+
+    def get_tuning(self):
+        return itp_get_tuning(self.h)
+
+    def set_tuning(self, pencil_w, split, row_tb, gram_ctas):
+        itp_set_tuning(self.h, pencil_w, split, row_tb, gram_ctas)
+
+    def autotune(self, order, tau):
+        return itp_autotune(self.h, order, tau)
 
     @property
     def kernel_launches(self):
