@@ -446,7 +446,9 @@ def main():
     clocks = ClockSampler(gpu_id)
     n0 = h.kernel_launches
     h.profile(True)
+    torch.cuda.nvtx.range_push("itp_timed_steps")   # lets a profiler select the timed launches
     dt, E = time_steps(h, stream, order, tau, args.steps, torch)
+    torch.cuda.nvtx.range_pop()
     prof = h.profile_read()
     h.profile(False)
     launches = h.kernel_launches - n0

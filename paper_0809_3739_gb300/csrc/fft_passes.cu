@@ -657,8 +657,11 @@ struct EpiTerm {
   }
 };
 
-// PLANE_HPSI: out = u + V * psi, in FP64 (out64) or in R (outr, with the
-// potential in R: the mixed path's subspace matrix is formed from FP32 data).
+// PLANE_HPSI: out = u + V * psi.  FP32 passes (the mixed path, whose
+// subspace matrix is formed from FP32 data) write FP32 to outr with the FP32
+// potential; FP64 passes write FP64 to out.  The choice is made at compile
+// time: a run-time branch let the compiler predicate the FP64 arm, whose
+// instructions then still occupied GB300's narrow FP64 pipe.
 template <typename R>
 struct EpiHpsi {
   using C = typename CplxOf<R>::type;
@@ -673,7 +676,7 @@ struct EpiHpsi {
     for (int j = 0; j < R2; ++j) {
       const int idx = (n1 + r1 * j) * npair + t;
       const C q = psi[idx];
-      if (outr) {
+      if constexpr (sizeof(R) == 4) {
         const C v = __ldg(&Vr[idx]);
         C h;
         h.x = a[j].x + v.x * q.x;
@@ -1224,6 +1227,9 @@ cudaError_t colpass_launch(const GridDesc& g, void* spec, const void* twy, int m
 template <typename R>
 cudaError_t launch_plane(const GridDesc& g, const PlaneArgs<R>& a, cudaStream_t st, int* nlaunch) {
   if (nlaunch) *nlaunch = 1;
+  // FP32 H psi passes write FP32 (potential and output in R)
+  if (a.mode == PLANE_HPSI && sizeof(R) == 4 && (!a.V_r || !a.phi_out))
+    return cudaErrorInvalidValue;
   if (g.split_planes[sizeof(R) == 4 ? 0 : 1]) {
     // planes too large for one CTA: column passes for y, row passes for x
     cudaError_t e = cudaSuccess;
