@@ -391,42 +391,49 @@ constexpr int kApplyNT = 32;                          // points per tile
 constexpr int kMBytes = 128 * 128 * 4;                // one part of M
 constexpr int kXTileBytes = kApplyNT * 128 * 4;       // one part of an X tile
 
+// Thread L of the CTA owns the group (4 points, 4 states) n4 = L & 7,
+// k4 = L >> 3 of a tile: four 16-byte loads along the point axis (one per
+// state row), held in registers; then a 4x4 register transpose and four
+// 16-byte shared stores (one per point, its 4 states = one core-matrix
+// row).  Loading is split from storing so that the next tile's loads are in
+// flight while the current tile is multiplied and written back.
+static_assert(kTcThreads == 256, "one (4 points, 4 states) group per thread");
 template <typename TX>
-__device__ __forceinline__ void stage_points(const TX* __restrict__ X, int m, long long N,
-                                             long long p0, uint32_t hi_base, uint32_t lo_base) {
-  // 256 groups of (4 points, 4 states): four 16-byte loads along the point
-  // axis (one per state row), a 4x4 register transpose, four 16-byte shared
-  // stores (one per point, its 4 states = one core-matrix row).
-  for (int L = threadIdx.x; L < 256; L += kTcThreads) {
-    const int n4 = L & 7, k4 = L >> 3;   // k4 in 0..31
-    const long long p = p0 + 4 * n4;
-    float v[4][4];
+__device__ __forceinline__ void load_points(const TX* __restrict__ X, int m, long long N,
+                                            long long p0, float (&v)[4][4]) {
+  const int L = threadIdx.x;
+  const int n4 = L & 7, k4 = L >> 3;   // k4 in 0..31
+  const long long p = p0 + 4 * n4;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int k = 4 * k4 + e;
+  for (int e = 0; e < 4; ++e) {
+    const int k = 4 * k4 + e;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) v[e][q] = 0.f;
-      if (k < m) {
-        const TX* src = X + (long long)k * N + p;
-        if (p + 3 < N) {
-          ld4(src, v[e]);
-        } else {
+    for (int q = 0; q < 4; ++q) v[e][q] = 0.f;
+    if (k < m) {
+      const TX* src = X + (long long)k * N + p;
+      if (p + 3 < N) {
+        ld4(src, v[e]);
+      } else {
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            if (p + q < N) v[e][q] = ldf(src + q);
-        }
+        for (int q = 0; q < 4; ++q)
+          if (p + q < N) v[e][q] = ldf(src + q);
       }
     }
+  }
+}
+__device__ __forceinline__ void store_points(const float (&v)[4][4], uint32_t hi_base,
+                                             uint32_t lo_base) {
+  const int L = threadIdx.x;
+  const int n4 = L & 7, k4 = L >> 3;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int n = 4 * n4 + q;
-      uint32_t h[4], l[4];
+  for (int q = 0; q < 4; ++q) {
+    const int n = 4 * n4 + q;
+    uint32_t h[4], l[4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) split_tf32(v[e][q], h[e], l[e]);
-      const uint32_t off = (uint32_t)(((n >> 3) * 32 + k4) * 128 + (n & 7) * 16);
-      st_shared_v4(hi_base + off, h[0], h[1], h[2], h[3]);
-      st_shared_v4(lo_base + off, l[0], l[1], l[2], l[3]);
-    }
+    for (int e = 0; e < 4; ++e) split_tf32(v[e][q], h[e], l[e]);
+    const uint32_t off = (uint32_t)(((n >> 3) * 32 + k4) * 128 + (n & 7) * 16);
+    st_shared_v4(hi_base + off, h[0], h[1], h[2], h[3]);
+    st_shared_v4(lo_base + off, l[0], l[1], l[2], l[3]);
   }
 }
 
@@ -516,10 +523,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const long long ntiles = (N + kApplyNT - 1) / kApplyNT;
   int local = 0;
   long long prev_tile = -1;
+  float cur[4][4], nxt[4][4];
+  if ((long long)blockIdx.x < ntiles) load_points(X, m, N, (long long)blockIdx.x * kApplyNT, cur);
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++local) {
     const int s = local & 1;
     if (local >= 2) mbar_wait(&bar[s], (uint32_t)(((local - 2) >> 1) & 1), status);
-    stage_points(X, m, N, tile * kApplyNT, xpart(s, 0), xpart(s, 1));
+    store_points(cur, xpart(s, 0), xpart(s, 1));
+    const long long next = tile + gridDim.x;
+    if (next < ntiles) load_points(X, m, N, next * kApplyNT, nxt);   // in flight meanwhile
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -547,6 +558,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       apply_epilogue(tmem + (uint32_t)(ps * kApplyNT), ostage, m, Y, N, prev_tile * kApplyNT);
     }
     prev_tile = tile;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cur[e][q] = nxt[e][q];
   }
   if (prev_tile >= 0) {
     const int ps = (local - 1) & 1;
