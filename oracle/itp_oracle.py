@@ -35,8 +35,8 @@ import numpy as np
 __all__ = [
     "mp_coefficients", "mp_coefficients_float", "kinetic_k2", "t2", "t2_power",
     "t2k", "romberg_t6", "overlap", "cholesky_orthonormalize", "apply_h",
-    "subspace_matrix", "energies", "itp_step", "solve",
-    "propagator_eigenvalue", "fft_count",
+    "subspace_matrix", "energies", "itp_step", "solve", "residual_h", "residual_e",
+    "solve_adaptive", "propagator_eigenvalue", "fft_count",
 ]
 
 
@@ -182,6 +182,14 @@ def residual_h(Psi, HPsi, E, dV):
     return ((HPsi - E[:, None] * Psi) ** 2).sum(axis=1) * dV
 
 
+def residual_e(Phi, Psi, E, tau, dV):
+    """R^E_j = sum_r |phi_j - exp(-tau E_j) psi_j|^2 dV with phi_j = T_2k(tau)
+    psi_j: the variance of psi_j with respect to the evolution operator
+    (Sec. III; the paper's exp(eps E) with eps = -tau, E_j for E_i, and the
+    volume element so that the value does not depend on the grid)."""
+    return ((Phi - np.exp(-tau * np.asarray(E))[:, None] * Psi) ** 2).sum(axis=1) * dV
+
+
 # ---------------------------------------------------------------------------
 def propagate(Psi, V, grid, order: int, tau: float):
     """Phi = T_2k(tau) Psi for every row of Psi (Eq. 3), k = order/2."""
@@ -214,6 +222,65 @@ def solve(Psi0, V, grid, order, tau, n_report, tol=1e-10, max_iter=1000,
             return E, Psi, it
         E_prev = E
     return E, Psi, max_iter
+
+
+def solve_adaptive(Psi0, V, grid, order, tau0, reduce, gamma, n_report, max_steps=200,
+                   max_levels=12):
+    """The adaptive iteration of Sec. III.
+
+    The initial states are orthonormalised (Eq. 4) and their diagonal
+    energies E_j = (psi_j|H|psi_j) dV taken.  Then, at a fixed tau (first
+    tau0), steps repeat: the states not yet converged are propagated (Eq. 3),
+    R^E_j is evaluated for them, all states are orthonormalised (Eq. 4) and
+    the diagonal energies taken again.  A state has converged at this tau
+    once R^E_j < gamma tau^2 / 10: for small tau, phi_j - exp(-tau E_j) psi_j
+    = -tau (H - E_j) psi_j + O(tau^2), so R^E_j / tau^2 is on the scale of
+    R^H_j, and one bound gamma serves both tests as the text has it (with
+    R^E_j < gamma literally, a reduced tau passes the test after one step
+    whatever R^H_j is, and the iteration stalls); the factor 1/10 makes the
+    states that pass it pass the final R^H_j < gamma too, instead of ending
+    each level just above it.  The states kept fixed are the leading ones up to the
+    first unconverged state, since a fixed state must precede the propagated
+    ones in the Cholesky order of Eq. (4) to stay unchanged.  When the first
+    n_report states have converged (or after max_steps steps), R^H_j is
+    evaluated for the current states: if R^H_j < gamma for all j < n_report
+    the iteration ends; else tau *= reduce and the steps repeat from the
+    current states, all of them propagated again.
+
+    Returns a dict: E (Ritz values), Psi (Ritz vectors), RH (R^H_j of the
+    last basis), levels = [(tau, steps, propagated state-steps), ...] and
+    converged (R^H below gamma before max_levels levels).
+    """
+    m = np.asarray(Psi0).shape[0]
+    Psi, _ = cholesky_orthonormalize(np.array(Psi0, dtype=np.float64), grid.dV)
+    E, Psi, HPsi = energies(Psi, V, grid, ritz=False)
+    tau = tau0
+    levels = []
+    RH = residual_h(Psi, HPsi, E, grid.dV)
+    converged = False
+    for _ in range(max_levels):
+        c = 0
+        steps = props = 0
+        while steps < max_steps and c < n_report:
+            Phi = Psi.copy()
+            Phi[c:] = propagate(Psi[c:], V, grid, order, tau)
+            RE = residual_e(Phi[c:], Psi[c:], E[c:], tau, grid.dV)
+            props += m - c
+            steps += 1
+            Psi, _ = cholesky_orthonormalize(Phi, grid.dV)
+            E, Psi, HPsi = energies(Psi, V, grid, ritz=False)
+            j = 0
+            while j < len(RE) and RE[j] < 0.1 * gamma * tau * tau:
+                j += 1
+            c += j
+        RH = residual_h(Psi, HPsi, E, grid.dV)
+        levels.append((tau, steps, props))
+        if np.all(RH[:n_report] < gamma):
+            converged = True
+            break
+        tau *= reduce
+    E, Psi, _ = energies(Psi, V, grid, ritz=True)
+    return dict(E=E, Psi=Psi, RH=RH, levels=levels, converged=converged)
 
 
 def propagator_eigenvalue(psi, V, grid, order, tau):

@@ -265,3 +265,54 @@ def test_ho_grid_spectrum_128_closed_shells():
     assert len(want) == 120
     assert np.max(np.abs(E[:120] - want)) < 1e-11
     assert abs(E[120] - 9.5) < 1e-11
+
+
+# --- the adaptive iteration of Sec. III (R^E, R^H, tau schedule) --------------
+def _dense_eigenpairs(g, V, count):
+    H = D.dense_hamiltonian(g, V)
+    w, U = np.linalg.eigh(H)
+    # normalise as sum psi^2 dV = 1
+    return H, w[:count], U[:, :count].T / np.sqrt(g.dV)
+
+
+def test_residuals_vanish_on_exact_eigenpairs_and_follow_the_closed_form():
+    """On exact eigenvectors of the dense grid Hamiltonian: R^H_j = 0, and
+    with the exact evolution operator e^{-tau H} (dense, from the DFT
+    definition) R^E_j = 0; shifting E_j by delta gives R^H_j = delta^2 and
+    R^E_j = (e^{-tau E_j} - e^{-tau (E_j + delta)})^2 exactly (sign of the
+    exponent and the pairing of E_j with psi_j are what this fixes)."""
+    g, V = _tiny_wells()
+    H, E, Psi = _dense_eigenpairs(g, V, 4)
+    HPsi = Psi @ H.T
+    assert np.max(O.residual_h(Psi, HPsi, E, g.dV)) < 1e-20
+    tau = 0.3
+    w, U = np.linalg.eigh(H)
+    expH = (U * np.exp(-tau * w)) @ U.T
+    Phi = Psi @ expH.T
+    assert np.max(O.residual_e(Phi, Psi, E, tau, g.dV)) < 1e-24
+    delta = np.array([1e-3, -2e-3, 5e-4, 0.0])
+    np.testing.assert_allclose(O.residual_h(Psi, HPsi, E + delta, g.dV), delta ** 2,
+                               rtol=1e-8, atol=1e-24)
+    want = (np.exp(-tau * E) - np.exp(-tau * (E + delta))) ** 2
+    np.testing.assert_allclose(O.residual_e(Phi, Psi, E + delta, tau, g.dV), want,
+                               rtol=1e-7, atol=1e-24)
+
+
+@pytest.mark.parametrize("order,gamma", [(8, 1e-12), (12, 1e-16)])
+def test_adaptive_iteration_reaches_the_oscillator_spectrum(order, gamma):
+    """The adaptive iteration ends with R^H_j < gamma, halves tau between
+    levels, and its Ritz values are the exact grid spectrum (separable 1D
+    dense eigenvalues) to within what R^H bounds: |E - E_ref| <= sqrt(R^H)
+    for a normalised state."""
+    g = cubic(16, 12.0)
+    V = harmonic_potential(g)
+    E_ref = D.ho_grid_spectrum(g, 4)
+    psi0 = normal_states(4, g.n_points, seed=7)
+    r = O.solve_adaptive(psi0, V, g, order, 0.5, 0.5, gamma, 4)
+    assert r["converged"]
+    assert np.all(r["RH"][:4] < gamma)
+    taus = [lv[0] for lv in r["levels"]]
+    assert taus == [0.5 * 0.5 ** i for i in range(len(taus))]
+    assert np.max(np.abs(r["E"] - E_ref)) < 2 * np.sqrt(gamma)
+    # selective propagation: the converged leading states stop being propagated
+    assert sum(lv[2] for lv in r["levels"]) < 4 * sum(lv[1] for lv in r["levels"])
