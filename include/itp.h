@@ -148,6 +148,36 @@ int itp_step(itp_handle h, int order, double tau, int flags, double* E_host);
 int itp_polish(itp_handle h, int order, double tau, double tol, int max_steps, int* steps_out,
                double* E_host);
 
+/* The adaptive iteration of Sec. III.  The states are orthonormalised and
+ * their energies E_j = (psi_j|H|psi_j) dV taken; then, at a fixed time step
+ * (first tau0), steps repeat: propagate the states not yet converged, take
+ * their variance with respect to the evolution operator
+ *     R^E_j = sum_r |T_2k(tau) psi_j - exp(-tau E_j) psi_j|^2 dV,
+ * orthonormalise all states (Eq. 4) and take the energies again.  A state
+ * counts as converged at this tau once R^E_j < gamma tau^2 / 10 (R^E is
+ * about tau^2 times R^H for small tau); the leading converged states are no
+ * longer propagated (they precede the others in the Cholesky order, so the
+ * orthonormalisation keeps them).  When the n_states wanted states have
+ * converged, or after max_steps steps, the variance with respect to H
+ *     R^H_j = sum_r |H psi_j - E_j psi_j|^2 dV
+ * is taken: if R^H_j < gamma for every wanted state the iteration ends,
+ * else tau *= reduce (0 < reduce < 1; the paper uses 0.5, and 0.9 for its
+ * figures) and the steps repeat from the current states.  At the end the
+ * states are rotated onto the Ritz vectors.
+ *   levels_out   (nullable) number of time steps used
+ *   level_stats  (nullable) [max_levels][3] doubles: tau, steps at that
+ *                tau, propagated state-steps at that tau
+ *   RH_host      (nullable) the m values R^H_j of the last basis
+ *   E_host       (nullable) the m Ritz values at the end
+ * Runs in the handle's precision (ITP_MIXED: FP32 passes, whose rounding,
+ * amplified by the kinetic energy of the grid's highest modes, sets a floor
+ * near 1e-8 for R^H at a 0.5 bohr spacing; ITP_FP64: FP64).  Synchronises.  Returns
+ * ITP_OK, or ITP_ERR_NOCONV (outputs filled) if R^H stayed above gamma for
+ * max_levels time steps. */
+int itp_solve_adaptive(itp_handle h, int order, double tau0, double reduce, double gamma,
+                       int max_steps, int max_levels, int* levels_out, double* level_stats,
+                       double* RH_host, double* E_host);
+
 /* Wait for the handle's stream; returns a pending device status. */
 int itp_synchronize(itp_handle h);
 

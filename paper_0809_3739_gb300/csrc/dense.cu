@@ -466,6 +466,62 @@ __global__ void diag_kernel(const double* __restrict__ H, int m, double* __restr
 }
 
 // ---------------------------------------------------------------------------
+// Residual norms of the adaptive iteration (Sec. III):
+//   out_j = dV * sum_p (A[j][p] - c_j B[j][p])^2,
+// c_j = exp(scale E_j) (mode 1: R^E with A = T psi, B = psi, scale = -tau) or
+// c_j = E_j (mode 0: R^H with A = H psi, B = psi).  Chunks of points per
+// CTA, the per-thread sums in the precision of the data, the rest in FP64,
+// partial sums combined in a fixed order.
+template <typename T> struct Vec4Of;
+template <> struct Vec4Of<float> { using type = float4; static constexpr int W = 4; };
+template <> struct Vec4Of<double> { using type = double2; static constexpr int W = 2; };
+
+__device__ __forceinline__ float sqdiff_sum(const float4 a, const float4 b, float c) {
+  const float d0 = a.x - c * b.x, d1 = a.y - c * b.y, d2 = a.z - c * b.z, d3 = a.w - c * b.w;
+  return d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
+}
+__device__ __forceinline__ double sqdiff_sum(const double2 a, const double2 b, double c) {
+  const double d0 = a.x - c * b.x, d1 = a.y - c * b.y;
+  return d0 * d0 + d1 * d1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) residual_partial_kernel(
+    const T* __restrict__ A, const T* __restrict__ B, const double* __restrict__ E,
+    double scale, int mode, long long N, int chunks, double* __restrict__ partial) {
+  using V = typename Vec4Of<T>::type;
+  constexpr int W = Vec4Of<T>::W;
+  const int j = blockIdx.y, c = blockIdx.x;
+  const T cj = (T)(mode ? exp(scale * E[j]) : E[j]);
+  const long long nv = N / W;
+  const long long per = (nv + chunks - 1) / chunks;
+  const long long v0 = (long long)c * per, v1 = min(nv, v0 + per);
+  const V* a = reinterpret_cast<const V*>(A + (long long)j * N);
+  const V* b = reinterpret_cast<const V*>(B + (long long)j * N);
+  T acc = 0;
+  for (long long v = v0 + threadIdx.x; v < v1; v += blockDim.x) acc += sqdiff_sum(a[v], b[v], cj);
+  double s = (double)acc;
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double ws[8];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    partial[(long long)j * chunks + c] = t;
+  }
+}
+
+__global__ void residual_final_kernel(const double* __restrict__ partial, int chunks, int m,
+                                      double dV, double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  double t = 0.0;
+  for (int c = 0; c < chunks; ++c) t += partial[(long long)j * chunks + c];
+  out[j] = t * dV;
+}
+
+// ---------------------------------------------------------------------------
 // Y = M X.  Persistent CTAs over tiles of 32 points; M (as TC) stays in
 // shared memory.  512 threads: tx = point in tile, ty = row group (16 rows).
 constexpr int kApplyPT = 32;
@@ -574,6 +630,23 @@ cudaError_t launch_bisect(const double* work, int m, double* E, cudaStream_t st)
   bisect_kernel<<<m, 32, 0, st>>>(work, work + m, m, E);
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_residual_norms(const T* A, const T* B, const double* E, double scale,
+                                  int mode, int m, long long N, double dV, int chunks,
+                                  double* partial, double* out, cudaStream_t st) {
+  if (m < 1 || chunks < 1 || (N % Vec4Of<T>::W)) return cudaErrorInvalidValue;
+  residual_partial_kernel<T><<<dim3(chunks, m), 256, 0, st>>>(A, B, E, scale, mode, N, chunks,
+                                                              partial);
+  residual_final_kernel<<<(m + 127) / 128, 128, 0, st>>>(partial, chunks, m, dV, out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_residual_norms<float>(const float*, const float*, const double*,
+                                                  double, int, int, long long, double, int,
+                                                  double*, double*, cudaStream_t);
+template cudaError_t launch_residual_norms<double>(const double*, const double*, const double*,
+                                                   double, int, int, long long, double, int,
+                                                   double*, double*, cudaStream_t);
 
 cudaError_t launch_diag(const double* H, int m, double* E, cudaStream_t st) {
   diag_kernel<<<1, 128, 0, st>>>(H, m, E);

@@ -70,6 +70,7 @@ struct itp_grid {
   int* status = nullptr;      // device status word
   int* status_host = nullptr; // pinned
   double* E_host_pinned = nullptr;
+  double* res_dev = nullptr;  // [2m] residual norms of the adaptive iteration
   long long launches = 0;
   std::string err;
   bool own_stream = false;    // created by the library (no stream given)
@@ -303,7 +304,7 @@ int prepare_tables(itp_handle h, Lane<R>& L, int k, double tau) {
 // keeps every term's spectrum in its own workspace, writes each term's FP32
 // contribution c_i f u_i over it, and sums the contributions once in FP64.
 template <typename R>
-int propagate_lane(itp_handle h, int k, double tau) {
+int propagate_lane(itp_handle h, int k, double tau, int s0 = 0) {
   Lane<R>& L = lane_of<R>(h);
   ITP_TRY(prepare_tables<R>(h, L, k, tau));
   const GridDesc& g = h->g;
@@ -319,12 +320,18 @@ int propagate_lane(itp_handle h, int k, double tau) {
       }
     }
   }
+  // states s0..m-1 only (the leading s0 states are kept fixed)
+  const int ms = h->m - s0;
+  const long long so = s0;
+  auto at_state = [&](void* w) {
+    return static_cast<void*>(static_cast<char*>(w) + so * g.n_half * 2 * sizeof(R));
+  };
   TermSumArgs ts{};
   for (int i = 1; i <= k; ++i) {
-    void* work = fused ? L.work_terms[i - 1] : L.work;
+    void* work = at_state(fused ? L.work_terms[i - 1] : L.work);
     PlaneArgs<R> pa{};
-    pa.m = h->m;
-    pa.in_real = L.psi;
+    pa.m = ms;
+    pa.in_real = L.psi + so * g.n_points;
     pa.spec = work;
     pa.twx = L.twx;
     pa.twy = L.twy;
@@ -333,7 +340,7 @@ int propagate_lane(itp_handle h, int k, double tau) {
     ITP_LAUNCH(h, ITP_KERNEL_PLANE_FWD, plane_counted<R>(h, pa));
     PencilArgs<R> pe{};
     pe.mode = PENCIL_PROPAGATE;
-    pe.m = h->m;
+    pe.m = ms;
     pe.spec = work;
     pe.kx_tab = L.ktab + (i - 1) * tl;
     pe.ky_tab = pe.kx_tab + g.nxh;
@@ -366,21 +373,21 @@ int propagate_lane(itp_handle h, int k, double tau) {
     pc.mode = PLANE_COMBINE;
     pc.f_in = nullptr;
     pc.f_out = L.f_half[i - 1];
-    pc.acc = h->acc;
+    pc.acc = h->acc + so * g.n_points;
     pc.coef = mp_coefficient(i, k);
     pc.acc_init = (i == 1);
     // the mixed path keeps the sum in FP64 and rounds the finished phi once
-    pc.phi_out = (sizeof(R) == 4 && i == k) ? L.psi_tmp : nullptr;
+    pc.phi_out = (sizeof(R) == 4 && i == k) ? L.psi_tmp + so * g.n_points : nullptr;
     ITP_LAUNCH(h, ITP_KERNEL_PLANE_COMBINE, plane_counted<R>(h, pc));
   }
   if (fused) {
     // phi = sum_i c_i f u_i in FP64 over the FP32 contributions
-    ts.m = h->m;
+    ts.m = ms;
     ts.k = k;
     ts.nz = g.nz;
     ts.plane_pts = g.nx * g.ny;
     ts.plane_pitch = 2LL * g.ny * g.nxh;
-    ts.phi_out = reinterpret_cast<float*>(L.psi_tmp);
+    ts.phi_out = reinterpret_cast<float*>(L.psi_tmp + so * g.n_points);
     ITP_LAUNCH(h, ITP_KERNEL_OTHER, launch_term_sum(ts, h->st));
   }
   return ITP_OK;
@@ -746,6 +753,92 @@ int autotune_lane(itp_handle h, int k, double tau, std::string& rep) {
   return ITP_OK;
 }
 
+// ---- the adaptive iteration of Sec. III -------------------------------------------
+// Residual norms of rows s0..m-1: mode 1 R^E (A = T psi, coefficient
+// exp(-tau E_j)), mode 0 R^H (A = H psi, coefficient E_j); into out[s0..].
+template <typename R>
+int residual_rows(itp_handle h, const R* A, const R* B, int mode, double tau, int s0,
+                  double* out) {
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  const int rows = h->m - s0;
+  const int chunks = std::max(1, std::min(2 * sms, (2 * sms * h->m) / rows));
+  const long long N = h->g.n_points;
+  ITP_LAUNCH(h, ITP_KERNEL_OTHER,
+             launch_residual_norms<R>(A + (long long)s0 * N, B + (long long)s0 * N,
+                                      h->E_dev + s0, -tau, mode, rows, N, h->dV, chunks,
+                                      h->partial, out + s0, h->st));
+  return ITP_OK;
+}
+
+template <typename R>
+int solve_adaptive_lane(itp_handle h, int k, double tau0, double reduce, double gamma,
+                        int max_steps, int max_levels, int* levels_out, double* stats,
+                        double* RH_host, double* E_host, bool* converged) {
+  Lane<R>& L = lane_of<R>(h);
+  const int m = h->m, n = h->n;
+  const long long N = h->g.n_points;
+  // the propagated block: FP32 psi_tmp (mixed) or the FP64 accumulator
+  R* phi = sizeof(R) == 4 ? L.psi_tmp : reinterpret_cast<R*>(h->acc);
+  const size_t row = (size_t)N * sizeof(R);
+  if (!h->res_dev) ITP_CUDA(h, cudaMalloc(&h->res_dev, 2 * (size_t)m * sizeof(double)));
+  double* RE_dev = h->res_dev;
+  double* RH_dev = h->res_dev + m;
+  std::vector<double> RE(m), RH(m, 0.0);
+  // orthonormalise the initial states and take their energies
+  ITP_CUDA(h, cudaMemcpyAsync(phi, L.psi, (size_t)m * row, cudaMemcpyDeviceToDevice, h->st));
+  ITP_TRY(orthonormalize_lane<R>(h));
+  ITP_TRY(energies_lane<R>(h, 0));
+  double tau = tau0;
+  int level = 0;
+  *converged = false;
+  for (; level < max_levels; ++level) {
+    int c = 0, steps = 0;
+    long long props = 0;
+    while (steps < max_steps && c < n) {
+      // fixed leading states enter the orthonormalisation as they are
+      if (c > 0)
+        ITP_CUDA(h, cudaMemcpyAsync(phi, L.psi, (size_t)c * row, cudaMemcpyDeviceToDevice,
+                                    h->st));
+      ITP_TRY(propagate_lane<R>(h, k, tau, c));
+      ITP_TRY(residual_rows<R>(h, phi, L.psi, 1, tau, c, RE_dev));
+      ITP_TRY(orthonormalize_lane<R>(h));
+      ITP_TRY(energies_lane<R>(h, 0));
+      ITP_CUDA(h, cudaMemcpyAsync(RE.data() + c, RE_dev + c, (size_t)(m - c) * sizeof(double),
+                                  cudaMemcpyDeviceToHost, h->st));
+      ITP_TRY(collect_status(h));
+      ++steps;
+      props += m - c;
+      int j = c;
+      while (j < m && RE[j] < 0.1 * gamma * tau * tau) ++j;
+      c = j;
+    }
+    // R^H of the current basis: H psi is where the energies left it
+    ITP_TRY(residual_rows<R>(h, phi, L.psi, 0, 0.0, 0, RH_dev));
+    ITP_CUDA(h, cudaMemcpyAsync(RH.data(), RH_dev, (size_t)m * sizeof(double),
+                                cudaMemcpyDeviceToHost, h->st));
+    ITP_TRY(collect_status(h));
+    if (stats) {
+      stats[3 * level] = tau;
+      stats[3 * level + 1] = steps;
+      stats[3 * level + 2] = (double)props;
+    }
+    bool done = true;
+    for (int j = 0; j < n; ++j) done = done && RH[j] < gamma;
+    if (done) {
+      *converged = true;
+      ++level;
+      break;
+    }
+    tau *= reduce;
+  }
+  if (levels_out) *levels_out = level;
+  if (RH_host) memcpy(RH_host, RH.data(), (size_t)m * sizeof(double));
+  // rotate onto the Ritz vectors and report the Ritz values
+  h->have_phi = false;
+  return do_energies(h, E_host, ITP_RITZ);
+}
+
 }  // namespace
 
 // A batch of independent problems: one handle (and stream) per problem and
@@ -926,6 +1019,7 @@ void itp_destroy(itp_handle h) {
   cudaFree(h->status);
   cudaFreeHost(h->status_host);
   cudaFreeHost(h->E_host_pinned);
+  cudaFree(h->res_dev);
   for (auto& e : h->prof_events) {
     cudaEventDestroy(e.start);
     cudaEventDestroy(e.stop);
@@ -1249,6 +1343,32 @@ int itp_autotune(itp_handle h, int order, double tau, int* tuning, char* report,
     memcpy(report, rep.data(), n);
     report[n] = 0;
   }
+  return ITP_OK;
+}
+
+int itp_solve_adaptive(itp_handle h, int order, double tau0, double reduce, double gamma,
+                       int max_steps, int max_levels, int* levels_out, double* level_stats,
+                       double* RH_host, double* E_host) {
+  ITP_TRY(check_ready(h, true));
+  if (order < 2 || order > 2 * kMaxTerms || (order & 1))
+    return fail(h, ITP_ERR_ARG, "order must be even, 2..%d (got %d)", 2 * kMaxTerms, order);
+  if (!(tau0 > 0) || !std::isfinite(tau0) || !(reduce > 0 && reduce < 1) || !(gamma > 0) ||
+      max_steps < 1 || max_levels < 1)
+    return fail(h, ITP_ERR_ARG, "bad adaptive-iteration arguments");
+  if (levels_out) *levels_out = 0;
+  bool converged = false;
+  if (h->precision == ITP_MIXED) {
+    ITP_TRY(switch_lane<float>(h));
+    ITP_TRY(solve_adaptive_lane<float>(h, order / 2, tau0, reduce, gamma, max_steps,
+                                       max_levels, levels_out, level_stats, RH_host, E_host,
+                                       &converged));
+  } else {
+    ITP_TRY(solve_adaptive_lane<double>(h, order / 2, tau0, reduce, gamma, max_steps,
+                                        max_levels, levels_out, level_stats, RH_host, E_host,
+                                        &converged));
+  }
+  if (!converged)
+    return fail(h, ITP_ERR_NOCONV, "R^H above gamma after %d levels", max_levels);
   return ITP_OK;
 }
 

@@ -136,6 +136,13 @@ cudaError_t launch_jacobi_eigh(const double* H, int m, double* E, double* Rt, do
 // tridiagonalisation into work = (d[m], e[m]), then bisection into E.
 cudaError_t launch_tridiag(const double* H, int m, double* work, cudaStream_t st);
 cudaError_t launch_bisect(const double* work, int m, double* E, cudaStream_t st);
+// out_j = dV sum_p (A[j][p] - c_j B[j][p])^2 over N points (N a multiple of
+// 4), c_j = exp(scale E_j) (mode 1) or E_j (mode 0); partial: m * chunks
+// doubles of scratch.  The residuals R^E (mode 1) and R^H (mode 0).
+template <typename T>
+cudaError_t launch_residual_norms(const T* A, const T* B, const double* E, double scale,
+                                  int mode, int m, long long N, double dV, int chunks,
+                                  double* partial, double* out, cudaStream_t st);
 // E[j] = H[j][j]
 cudaError_t launch_diag(const double* H, int m, double* E, cudaStream_t st);
 // Y = M * X over all points: Y[i][p] = sum_k M[i][k] X[k][p]   (M lower

@@ -48,6 +48,7 @@ SIGNATURES = [
     ("itp_energies", _I, [_H, _PD, _I]),
     ("itp_step", _I, [_H, _I, _D, _I, _PD]),
     ("itp_polish", _I, [_H, _I, _D, _D, _I, ctypes.POINTER(_I), _PD]),
+    ("itp_solve_adaptive", _I, [_H, _I, _D, _D, _D, _I, _I, ctypes.POINTER(_I), _PD, _PD, _PD]),
     ("itp_synchronize", _I, [_H]),
     ("itp_last_error", ctypes.c_char_p, [_H]),
     ("itp_kernel_launches", ctypes.c_longlong, [_H]),
@@ -177,6 +178,21 @@ def itp_polish(h, order, tau, tol, max_steps, out: np.ndarray | None = None):
     _check(h, load().itp_polish(h, int(order), float(tau), float(tol), int(max_steps),
                                 ctypes.byref(steps), ptr))
     return steps.value
+
+
+def itp_solve_adaptive(h, m, order, tau0, reduce, gamma, max_steps=200, max_levels=12):
+    """Returns dict(E, RH, levels=[(tau, steps, propagated state-steps)], converged)."""
+    lv = _I(0)
+    stats = np.zeros((max_levels, 3), dtype=np.float64)
+    RH = np.empty(m, dtype=np.float64)
+    E = np.empty(m, dtype=np.float64)
+    code = load().itp_solve_adaptive(h, int(order), float(tau0), float(reduce), float(gamma),
+                                     int(max_steps), int(max_levels), ctypes.byref(lv),
+                                     stats.ctypes.data, RH.ctypes.data, E.ctypes.data)
+    if code not in (ITP_OK, ITP_ERR_NOCONV):
+        _check(h, code)
+    levels = [(float(t), int(s), int(p)) for t, s, p in stats[:lv.value]]
+    return {"E": E, "RH": RH, "levels": levels, "converged": code == ITP_OK}
 
 
 def itp_synchronize(h):
@@ -365,6 +381,10 @@ class ItpGrid:
 
     def synchronize(self):
         itp_synchronize(self.h)
+
+    def solve_adaptive(self, order, tau0, reduce, gamma, max_steps=200, max_levels=12):
+        return itp_solve_adaptive(self.h, self.m, order, tau0, reduce, gamma, max_steps,
+                                  max_levels)
 
     def get_tuning(self):
         return itp_get_tuning(self.h)
