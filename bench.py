@@ -308,6 +308,42 @@ def time_to_tol(P, precision, tol=1e-8, order=12, tau=0.5, n=120, guard=8,
             "max_abs_error_ha": err, "reached": err < tol}
 
 
+def adaptive_to_tol(P, precision, tol=1e-8, order=12, n=120, guard=8):
+    """The adaptive iteration of Sec. III (itp_solve_adaptive: tau 0.5,
+    halved between levels, converged leading states no longer propagated,
+    stop on R^H) on the time-to-tolerance problem (3D oscillator, 128^3,
+    box [-8,8)^3, n = 120 closed-shell states).  FP64: bound gamma = tol.
+    Mixed: FP32 levels down to gamma = 1e-6 (on this grid, spacing 0.125
+    bohr, the FP32 floor of R^H lies near 3e-7), then FP64 polish steps
+    until the energies change by less than tol / 10.  Wall time from itp_set_states; the error against the
+    exact n + 3/2 is measured after the clock stops."""
+    from itp_workloads import cubic, harmonic_potential, normal_states
+    g = cubic(128, 16.0)
+    V = harmonic_potential(g)
+    m = n + guard
+    psi = normal_states(m, g.n_points, seed=4321)
+    E_ref = ho_closed_shells(n)
+    h = P.ItpGrid(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, n, guard, precision)
+    h.set_potential(V)
+    h.synchronize()
+    t0 = time.perf_counter()
+    h.set_states(psi)
+    polish_steps = 0
+    if precision == P.ITP_MIXED:
+        r = h.solve_adaptive(order, 0.5, 0.5, 1e-6, max_steps=100, max_levels=2)
+        polish_steps, E = h.polish(order, 0.5 * 0.5 ** (len(r["levels"]) - 1), tol / 10, 20)
+    else:
+        r = h.solve_adaptive(order, 0.5, 0.5, tol, max_steps=100, max_levels=4)
+        E = r["E"]
+    h.synchronize()
+    dt = time.perf_counter() - t0
+    h.close()
+    err = float(np.max(np.abs(np.asarray(E)[:n] - E_ref)))
+    return {"seconds": dt, "levels": r["levels"], "adaptive_converged": r["converged"],
+            "max_RH": float(np.max(r["RH"][:n])), "fp64_polish_steps": polish_steps,
+            "max_abs_error_ha": err, "reached": err < tol}
+
+
 def batch_throughput(P, torch, steps, warmup, count=64, order=8, tau=0.25, seed=1000):
     """The batched workload: `count` independent random-well problems (grid
     edges from {32, 48, 64, 96}, n ~ U{8..64} states, 4-60 Gaussian wells),
@@ -400,6 +436,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance runs")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
+    ap.add_argument("--adaptive-fp64", action="store_true",
+                    help="also time the FP64 adaptive iteration (about two minutes)")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
@@ -579,6 +617,10 @@ def main():
                "mixed": time_to_tol(P, P.ITP_MIXED),
                "fp64": time_to_tol(P, P.ITP_FP64)}
         ttt["speedup_mixed_vs_fp64"] = ttt["fp64"]["seconds"] / ttt["mixed"]["seconds"]
+        # the same problem with the adaptive iteration of Sec. III
+        ttt["adaptive"] = {"mixed": adaptive_to_tol(P, P.ITP_MIXED)}
+        if args.adaptive_fp64:   # about two minutes on one GB300
+            ttt["adaptive"]["fp64"] = adaptive_to_tol(P, P.ITP_FP64)
 
     # ---- the batched workload: 64 independent problems, one graph per step ----
     batch = None
