@@ -344,6 +344,36 @@ def adaptive_to_tol(P, precision, tol=1e-8, order=12, n=120, guard=8):
             "max_abs_error_ha": err, "reached": err < tol}
 
 
+def order_sweep_small(P, orders=(2, 4, 6, 8, 10, 12), gamma=1e-10):
+    """Which order is fastest (the paper found 6 on one Itanium processor):
+    the adaptive iteration (tau 0.5, halved between levels, stop on R^H <
+    gamma) at each order on the 3D oscillator, 32^3 grid, box [-8,8)^3,
+    n = 10 + 2 guard states, FP64; wall time, steps and the error of the 10
+    energies against n + 3/2."""
+    from itp_workloads import cubic, harmonic_potential, normal_states
+    g = cubic(32, 16.0)
+    V = harmonic_potential(g)
+    psi = normal_states(12, g.n_points, seed=1234)
+    E_ref = ho_closed_shells(10)
+    out = {}
+    for order in orders:
+        h = P.ItpGrid(32, 32, 32, 16.0, 16.0, 16.0, 10, 2, P.ITP_FP64)
+        h.set_potential(V)
+        h.synchronize()
+        t0 = time.perf_counter()
+        h.set_states(psi)
+        r = h.solve_adaptive(order, 0.5, 0.5, gamma, max_steps=300, max_levels=10)
+        h.synchronize()
+        dt = time.perf_counter() - t0
+        h.close()
+        out[str(order)] = {"seconds": round(dt, 4), "levels": len(r["levels"]),
+                           "steps": sum(lv[1] for lv in r["levels"]),
+                           "final_tau": r["levels"][-1][0] if r["levels"] else None,
+                           "converged": r["converged"],
+                           "max_abs_error_ha": float(np.max(np.abs(r["E"][:10] - E_ref)))}
+    return out
+
+
 def batch_throughput(P, torch, steps, warmup, count=64, order=8, tau=0.25, seed=1000):
     """The batched workload: `count` independent random-well problems (grid
     edges from {32, 48, 64, 96}, n ~ U{8..64} states, 4-60 Gaussian wells),
@@ -552,6 +582,33 @@ def main():
              "ms_per_step": 1e3 * dt_graph / args.steps, "steps": args.steps}
     breakdown = {k: {"launches": v[0], "ms": round(v[1], 3),
                      "share": round(v[1] / total_prof, 4)} for k, v in kinds.items()}
+    # cost of one step at every order, and of the Romberg T_6 propagation
+    # (Eq. sixp) against the multi-product T_6 (same workload, graph steps)
+    order_cost = {}
+    for o in (2, 4, 6, 8, 10, 12):
+        for _ in range(2):
+            h.step_graph(o, tau)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(3):
+            h.step_graph(o, tau)
+        b.record(stream)
+        b.synchronize()
+        order_cost[str(o)] = round(a.elapsed_time(b) / 3, 3)
+    prop_ms = {}
+    for name, fn in (("multi_product_t6", lambda: h.propagate(6, tau)),
+                     ("romberg_t6", lambda: h.propagate_romberg6(tau))):
+        fn()
+        h.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(3):
+            fn()
+        b.record(stream)
+        b.synchronize()
+        prop_ms[name] = round(a.elapsed_time(b) / 3, 3)
     h.close()
 
     # ---- end to end through the C ABI with host buffers -----------------------
@@ -633,6 +690,10 @@ def main():
             batch["value"] *= world * batch["ms_per_step"] / float(v.item())
             batch["ms_per_step"] = float(v.item())
 
+    sweep = None
+    if not args.no_ttt:
+        sweep = order_sweep_small(P)
+
     # ---- CPU oracle on a bounded sample (rank 0, N = 1 only) -------------------
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
@@ -671,6 +732,9 @@ def main():
             "graph_replay": graph,
             "fp64_path": fp64,
             "time_to_tol": ttt,
+            "orders": {"ms_per_step_by_order": order_cost,
+                       "propagation_ms": prop_ms,
+                       "time_to_tol_by_order_ho32": sweep},
             "batch": batch,
             "e2e": e2e,
             "cpu_baseline": cpu,

@@ -148,6 +148,18 @@ int itp_step(itp_handle h, int order, double tau, int flags, double* E_host);
 int itp_polish(itp_handle h, int order, double tau, double tol, int max_steps, int* steps_out,
                double* E_host);
 
+/* Eq. (sixp), the Romberg-type sixth-order propagator that the paper sets
+ * against the multi-product expansion:
+ *     phi_j = -T_4(tau) psi_j / 15 + 16 T_4(tau/2)^2 psi_j / 15,
+ * T_4 the order-4 multi-product expansion (Eq. four).  It costs 9 complete
+ * FFT pairs per state where the multi-product T_6 costs 6.  With T_4 a sum
+ * of products (not time-symmetric) it cancels the tau^5 term only: its
+ * local error is tau^6, one order short of the multi-product T_6.  Same
+ * contract as itp_propagate (the propagated block is then orthonormalised
+ * by itp_orthonormalize); needs one extra state block of device memory,
+ * allocated at the first call. */
+int itp_propagate_romberg6(itp_handle h, double tau);
+
 /* The adaptive iteration of Sec. III.  The states are orthonormalised and
  * their energies E_j = (psi_j|H|psi_j) dV taken; then, at a fixed time step
  * (first tau0), steps repeat: propagate the states not yet converged, take

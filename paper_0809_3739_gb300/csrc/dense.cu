@@ -648,6 +648,25 @@ template cudaError_t launch_residual_norms<double>(const double*, const double*,
                                                    double, int, int, long long, double, int,
                                                    double*, double*, cudaStream_t);
 
+template <typename R>
+__global__ void axpby_kernel(R a, const R* __restrict__ X, R b, const R* Y, R* out,
+                             long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = fma(b, Y[i], a * X[i]);
+}
+
+template <typename R>
+cudaError_t launch_axpby(double a, const R* X, double b, const R* Y, R* out, long long n,
+                         cudaStream_t st) {
+  axpby_kernel<R><<<4 * 152, 256, 0, st>>>((R)a, X, (R)b, Y, out, n);
+  return cudaGetLastError();
+}
+template cudaError_t launch_axpby<float>(double, const float*, double, const float*, float*,
+                                         long long, cudaStream_t);
+template cudaError_t launch_axpby<double>(double, const double*, double, const double*,
+                                          double*, long long, cudaStream_t);
+
 cudaError_t launch_diag(const double* H, int m, double* E, cudaStream_t st) {
   diag_kernel<<<1, 128, 0, st>>>(H, m, E);
   return cudaGetLastError();

@@ -36,6 +36,7 @@ struct Lane {
   R* ktab = nullptr;         // per term: nxh + ny + nz propagation factors
   R* htab = nullptr;         // nxh + ny + nz kinetic values k^2/2
   R* Vr = nullptr;           // [N] potential in precision R (internal layout)
+  R* rom = nullptr;          // [m][N] scratch of the Romberg T_6 comparator (on demand)
   void* twx = nullptr;
   void* twy = nullptr;
   void* twz = nullptr;
@@ -258,6 +259,7 @@ void free_lane(Lane<R>& L) {
   cudaFree(L.ktab);
   cudaFree(L.htab);
   cudaFree(L.Vr);
+  cudaFree(L.rom);
   cudaFree(L.twx);
   cudaFree(L.twy);
   cudaFree(L.twz);
@@ -304,7 +306,8 @@ int prepare_tables(itp_handle h, Lane<R>& L, int k, double tau) {
 // keeps every term's spectrum in its own workspace, writes each term's FP32
 // contribution c_i f u_i over it, and sums the contributions once in FP64.
 template <typename R>
-int propagate_lane(itp_handle h, int k, double tau, int s0 = 0) {
+int propagate_lane(itp_handle h, int k, double tau, int s0 = 0, const R* in = nullptr,
+                   R* out = nullptr) {
   Lane<R>& L = lane_of<R>(h);
   ITP_TRY(prepare_tables<R>(h, L, k, tau));
   const GridDesc& g = h->g;
@@ -331,7 +334,7 @@ int propagate_lane(itp_handle h, int k, double tau, int s0 = 0) {
     void* work = at_state(fused ? L.work_terms[i - 1] : L.work);
     PlaneArgs<R> pa{};
     pa.m = ms;
-    pa.in_real = L.psi + so * g.n_points;
+    pa.in_real = (in ? in : L.psi) + so * g.n_points;
     pa.spec = work;
     pa.twx = L.twx;
     pa.twy = L.twy;
@@ -373,11 +376,11 @@ int propagate_lane(itp_handle h, int k, double tau, int s0 = 0) {
     pc.mode = PLANE_COMBINE;
     pc.f_in = nullptr;
     pc.f_out = L.f_half[i - 1];
-    pc.acc = h->acc + so * g.n_points;
+    pc.acc = (sizeof(R) == 8 && out ? reinterpret_cast<double*>(out) : h->acc) + so * g.n_points;
     pc.coef = mp_coefficient(i, k);
     pc.acc_init = (i == 1);
     // the mixed path keeps the sum in FP64 and rounds the finished phi once
-    pc.phi_out = (sizeof(R) == 4 && i == k) ? L.psi_tmp + so * g.n_points : nullptr;
+    pc.phi_out = (sizeof(R) == 4 && i == k) ? (out ? out : L.psi_tmp) + so * g.n_points : nullptr;
     ITP_LAUNCH(h, ITP_KERNEL_PLANE_COMBINE, plane_counted<R>(h, pc));
   }
   if (fused) {
@@ -387,7 +390,7 @@ int propagate_lane(itp_handle h, int k, double tau, int s0 = 0) {
     ts.nz = g.nz;
     ts.plane_pts = g.nx * g.ny;
     ts.plane_pitch = 2LL * g.ny * g.nxh;
-    ts.phi_out = reinterpret_cast<float*>(L.psi_tmp + so * g.n_points);
+    ts.phi_out = reinterpret_cast<float*>((out ? out : L.psi_tmp) + so * g.n_points);
     ITP_LAUNCH(h, ITP_KERNEL_OTHER, launch_term_sum(ts, h->st));
   }
   return ITP_OK;
@@ -837,6 +840,24 @@ int solve_adaptive_lane(itp_handle h, int k, double tau0, double reduce, double 
   // rotate onto the Ritz vectors and report the Ritz values
   h->have_phi = false;
   return do_energies(h, E_host, ITP_RITZ);
+}
+
+// ---- Eq. (sixp): the Romberg-type T_6 (a comparator of Eq. mcomp) ----------------
+// phi = -T_4(tau) psi / 15 + 16 T_4(tau/2)^2 psi / 15 with T_4 the order-4
+// multi-product expansion: three T_4 applications (9 T_2) against six T_2
+// for the multi-product T_6.
+template <typename R>
+int propagate_romberg6_lane(itp_handle h, double tau) {
+  Lane<R>& L = lane_of<R>(h);
+  const size_t bytes = (size_t)h->m * h->g.n_points * sizeof(R);
+  if (!L.rom) ITP_CUDA(h, cudaMalloc(&L.rom, bytes));
+  R* out = sizeof(R) == 4 ? L.psi_tmp : reinterpret_cast<R*>(h->acc);
+  ITP_TRY(propagate_lane<R>(h, 2, 0.5 * tau, 0, L.psi, L.rom));   // v = T_4(tau/2) psi
+  ITP_TRY(propagate_lane<R>(h, 2, 0.5 * tau, 0, L.rom, out));     // w = T_4(tau/2) v
+  ITP_TRY(propagate_lane<R>(h, 2, tau, 0, L.psi, L.rom));         // u = T_4(tau) psi
+  ITP_LAUNCH(h, ITP_KERNEL_OTHER, launch_axpby<R>(16.0 / 15.0, out, -1.0 / 15.0, L.rom, out,
+                                                  (long long)h->m * h->g.n_points, h->st));
+  return ITP_OK;
 }
 
 }  // namespace
@@ -1343,6 +1364,19 @@ int itp_autotune(itp_handle h, int order, double tau, int* tuning, char* report,
     memcpy(report, rep.data(), n);
     report[n] = 0;
   }
+  return ITP_OK;
+}
+
+int itp_propagate_romberg6(itp_handle h, double tau) {
+  ITP_TRY(check_ready(h, true));
+  if (!(tau > 0) || !std::isfinite(tau)) return fail(h, ITP_ERR_ARG, "tau must be > 0");
+  if (h->precision == ITP_MIXED) {
+    ITP_TRY(switch_lane<float>(h));
+    ITP_TRY(propagate_romberg6_lane<float>(h, tau));
+  } else {
+    ITP_TRY(propagate_romberg6_lane<double>(h, tau));
+  }
+  h->have_phi = true;
   return ITP_OK;
 }
 

@@ -143,6 +143,10 @@ template <typename T>
 cudaError_t launch_residual_norms(const T* A, const T* B, const double* E, double scale,
                                   int mode, int m, long long N, double dV, int chunks,
                                   double* partial, double* out, cudaStream_t st);
+// out = a X + b Y elementwise (out may alias X).
+template <typename R>
+cudaError_t launch_axpby(double a, const R* X, double b, const R* Y, R* out, long long n,
+                         cudaStream_t st);
 // E[j] = H[j][j]
 cudaError_t launch_diag(const double* H, int m, double* E, cudaStream_t st);
 // Y = M * X over all points: Y[i][p] = sum_k M[i][k] X[k][p]   (M lower

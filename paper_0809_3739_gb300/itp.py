@@ -48,6 +48,7 @@ SIGNATURES = [
     ("itp_energies", _I, [_H, _PD, _I]),
     ("itp_step", _I, [_H, _I, _D, _I, _PD]),
     ("itp_polish", _I, [_H, _I, _D, _D, _I, ctypes.POINTER(_I), _PD]),
+    ("itp_propagate_romberg6", _I, [_H, _D]),
     ("itp_solve_adaptive", _I, [_H, _I, _D, _D, _D, _I, _I, ctypes.POINTER(_I), _PD, _PD, _PD]),
     ("itp_synchronize", _I, [_H]),
     ("itp_last_error", ctypes.c_char_p, [_H]),
@@ -154,6 +155,10 @@ def itp_get_phi(h, out: np.ndarray):
 
 def itp_propagate(h, order: int, tau: float):
     _check(h, load().itp_propagate(h, int(order), float(tau)))
+
+
+def itp_propagate_romberg6(h, tau: float):
+    _check(h, load().itp_propagate_romberg6(h, float(tau)))
 
 
 def itp_orthonormalize(h):
@@ -355,6 +360,9 @@ class ItpGrid:
 
     def orthonormalize(self):
         itp_orthonormalize(self.h)
+
+    def propagate_romberg6(self, tau):
+        itp_propagate_romberg6(self.h, tau)
 
     def energies(self, ritz=True):
         """ritz: True (values + rotation), "values" (values only) or False
