@@ -18,6 +18,9 @@
  *  - Grid: nx*ny*nz points, each edge even and a product of two factors
  *    from {1,2,3,4,6,8,12,16} (2..256 points); box [-L/2, L/2) per axis,
  *    x_i = -L/2 + i*L/n; periodic.  Point index (z*ny + y)*nx + x.
+ *    nz = 1 makes the problem two-dimensional (the paper's second case, a
+ *    square array of quantum dots, Sec. III): the z transform is the
+ *    identity and k_z = 0; with lz = 1 the volume element is dx*dy.
  *  - States: a block of m = n_states + n_guard real states, row-major
  *    [m][nz][ny][nx] doubles on the host.  Guard states are propagated and
  *    orthonormalised like the others; they speed up the convergence of the

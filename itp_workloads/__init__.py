@@ -18,7 +18,9 @@ the Gaussian C60-like well stands in for it):
   * harmonic oscillator V = r^2/2 (hbar = m = 1, Hartree units);
   * C60-like well: 60 Gaussian wells of depth 2.0 Ha, width 0.8 bohr on the
     vertices of a truncated icosahedron scaled to radius 6.7 bohr;
-  * random Gaussian-well problems for the batched workload.
+  * random Gaussian-well problems for the batched workload;
+  * planar problems (nz = 1): the 2D oscillator and a square array of
+    quantum dots with the paper's sech well shape.
 """
 from __future__ import annotations
 
@@ -33,7 +35,8 @@ import numpy as np
 __all__ = [
     "philox4x32_10", "uniform53", "normal_states", "Grid", "grid_axes",
     "harmonic_potential", "truncated_icosahedron", "gaussian_wells_potential",
-    "c60_like_potential", "random_wells_problem", "supported_dim",
+    "c60_like_potential", "random_wells_problem", "supported_dim", "planar",
+    "harmonic_potential_2d", "quantum_dot_array",
 ]
 
 # ---------------------------------------------------------------------------
@@ -254,6 +257,36 @@ def c60_like_potential(g: Grid, depth: float = 2.0, sigma: float = 0.8,
                        radius: float = 6.7) -> np.ndarray:
     """Gaussian C60-like well: 60 wells on the truncated-icosahedron vertices."""
     return gaussian_wells_potential(g, truncated_icosahedron(radius), depth, sigma)
+
+
+def planar(nx: int, ny: int, lx: float, ly: float) -> Grid:
+    """A two-dimensional grid: nz = 1 and lz = 1, so the volume element is
+    dx*dy and the z coordinate plays no part (the potentials below for
+    planar problems depend on x and y only)."""
+    return Grid(nx, ny, 1, lx, ly, 1.0)
+
+
+def harmonic_potential_2d(g: Grid, omega: float = 1.0) -> np.ndarray:
+    """V = omega^2 (x^2 + y^2) / 2 on a planar grid, shape (1, ny, nx)."""
+    _, y, x = grid_axes(g)
+    return (0.5 * omega ** 2 * (y[:, None] ** 2 + x[None, :] ** 2))[None, :, :]
+
+
+def quantum_dot_array(g: Grid, n_side: int = 9, spacing: float = 3.0, depth: float = 2.0,
+                      width: float = 0.6) -> np.ndarray:
+    """The planar case of the method's demonstration: a square n_side x
+    n_side array of quantum dots centred in the box, each with the paper's
+    well shape V = -depth / cosh(|r - R|/width) (Hartree, bohr; the printed
+    strength and width are not usable, so depth and width are chosen here),
+    summed over the dots.  Shape (1, ny, nx)."""
+    _, y, x = grid_axes(g)
+    c = (np.arange(n_side) - 0.5 * (n_side - 1)) * spacing
+    V = np.zeros((g.ny, g.nx))
+    for cy in c:
+        for cx in c:
+            r = np.sqrt((y[:, None] - cy) ** 2 + (x[None, :] - cx) ** 2)
+            V -= depth / np.cosh(r / width)
+    return V[None, :, :]
 
 
 _TAG_WELLS = 0x3E11C0DE

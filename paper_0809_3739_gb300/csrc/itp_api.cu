@@ -911,10 +911,17 @@ int itp_create_grid(itp_handle* out, int nx, int ny, int nz, double lx, double l
     return code;
   };
   GridDesc& g = h->g;
+  // nz = 1: a 2D problem in the x-y plane (the z transform is the identity)
+  const bool planar = nz == 1;
+  if (planar) {
+    g.rz1 = 1;
+    g.rz2 = 1;
+  }
   if (!split_axis(nx, &g.rx1, &g.rx2) || !split_axis(ny, &g.ry1, &g.ry2) ||
-      !split_axis(nz, &g.rz1, &g.rz2))
+      (!planar && !split_axis(nz, &g.rz1, &g.rz2)))
     return bail(fail(h, ITP_ERR_ARG, "unsupported grid %dx%dx%d (edges even, 2..256, "
-                                     "a product of two of 1,2,3,4,6,8,12,16)", nx, ny, nz));
+                                     "a product of two of 1,2,3,4,6,8,12,16; nz may be 1)",
+                     nx, ny, nz));
   if (!(lx > 0 && ly > 0 && lz > 0))
     return bail(fail(h, ITP_ERR_ARG, "box lengths must be positive"));
   if (n_states < 1 || n_guard < 0 || n_states + n_guard > kMaxStates)

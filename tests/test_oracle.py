@@ -316,3 +316,33 @@ def test_adaptive_iteration_reaches_the_oscillator_spectrum(order, gamma):
     assert np.max(np.abs(r["E"] - E_ref)) < 2 * np.sqrt(gamma)
     # selective propagation: the converged leading states stop being propagated
     assert sum(lv[2] for lv in r["levels"]) < 4 * sum(lv[1] for lv in r["levels"])
+
+
+# --- the planar case (nz = 1): the 2D array of quantum dots ------------------
+def test_t2_matches_dense_operator_planar():
+    from itp_workloads import planar
+    g = planar(8, 6, 5.0, 4.0)
+    rng = np.random.default_rng(5)
+    V = rng.uniform(-1.0, 1.0, g.shape)
+    psi = rng.standard_normal(g.shape)
+    tau = 0.37
+    k2 = O.kinetic_k2(g.shape, (g.lz, g.ly, g.lx))
+    got = O.t2(psi, V, tau, k2).ravel()
+    want = D.dense_t2(g, V, tau) @ psi.ravel()
+    assert np.max(np.abs(got - want)) < 1e-12 * np.max(np.abs(want))
+
+
+def test_planar_oscillator_spectrum():
+    """2D oscillator: E = n_x + n_y + 1 with degeneracies 1, 2, 3 (the grid
+    spectrum is the sum of two 1D dense spectra and equals it to 1e-10 on a
+    32 x 32 grid in [-8, 8)^2), and the iteration converges to it."""
+    from itp_workloads import harmonic_potential_2d, planar
+    g = planar(32, 32, 16.0, 16.0)
+    V = harmonic_potential_2d(g)
+    x = -8.0 + 0.5 * np.arange(32)
+    e1 = np.linalg.eigvalsh(D.kinetic_1d(32, 16.0) + np.diag(0.5 * x ** 2))
+    grid_E = np.sort((e1[:, None] + e1[None, :]).ravel())[:6]
+    np.testing.assert_allclose(grid_E, [1, 2, 2, 3, 3, 3], atol=1e-10)
+    psi0 = normal_states(8, g.n_points, seed=21)
+    E, Psi, it = O.solve(psi0, V, g, 8, 0.4, n_report=6, tol=1e-12, max_iter=2000)
+    assert np.max(np.abs(E[:6] - grid_E)) < 1e-9

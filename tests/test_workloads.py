@@ -68,3 +68,17 @@ def test_native_generator_matches_numpy():
     a = W.normal_states(2, 4096, seed=77, problem=3, use_native=True)
     b = W.normal_states(2, 4096, seed=77, problem=3, use_native=False)
     assert np.array_equal(a, b)
+
+
+def test_quantum_dot_array_geometry():
+    from itp_workloads import planar, quantum_dot_array
+    g = planar(128, 128, 32.0, 32.0)
+    V = quantum_dot_array(g)
+    assert V.shape == (1, 128, 128)
+    # mirror symmetric about the box centre (grid point 64 is x = 0)
+    core = V[0, 1:, 1:]
+    np.testing.assert_allclose(core, core[::-1, :], atol=1e-12)
+    np.testing.assert_allclose(core, core[:, ::-1], atol=1e-12)
+    # the deepest points sit at dot centres: about -depth, plus the tails of
+    # the neighbours (sech decays as 2 exp(-r/w))
+    assert -2.2 < V.min() < -2.0
