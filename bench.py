@@ -374,6 +374,56 @@ def order_sweep_small(P, orders=(2, 4, 6, 8, 10, 12), gamma=1e-10):
     return out
 
 
+def planar_dots(P, torch, steps, warmup, order=12, tau=0.25):
+    """The paper's planar case: a 9 x 9 array of quantum dots (sech wells,
+    depth 2 Ha, width 0.6 bohr, spacing 3 bohr) on a 256 x 256 grid in a
+    32 bohr box, n = 81 (one state per dot) + 8 guard states.  Mixed steps
+    (graph replays) per second, and the FP64 adaptive iteration's wall time
+    to R^H < 1e-10 for the 81 states."""
+    from itp_workloads import normal_states, planar, quantum_dot_array
+    g = planar(256, 256, 32.0, 32.0)
+    V = quantum_dot_array(g)
+    n, guard = 81, 8
+    psi = normal_states(n + guard, g.n_points, seed=81)
+    stream = torch.cuda.Stream()
+    h = P.ItpGrid(256, 256, 1, 32.0, 32.0, 1.0, n, guard, P.ITP_MIXED,
+                  cuda_stream=stream.cuda_stream)
+    h.set_potential(V)
+    h.set_states(psi)
+    tuned, _ = h.autotune(order, tau)
+    for _ in range(warmup):
+        h.step_graph(order, tau)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        E = h.step_graph(order, tau)
+    b.record(stream)
+    b.synchronize()
+    dt = a.elapsed_time(b) / 1e3
+    h.close()
+    h = P.ItpGrid(256, 256, 1, 32.0, 32.0, 1.0, n, guard, P.ITP_FP64)
+    h.set_potential(V)
+    h.synchronize()
+    t0 = time.perf_counter()
+    h.set_states(psi)
+    r = h.solve_adaptive(order, 0.5, 0.5, 1e-10, max_steps=150, max_levels=3)
+    h.synchronize()
+    t_ad = time.perf_counter() - t0
+    h.close()
+    return {"workload": "9 x 9 quantum dots (sech wells, depth 2 Ha, width 0.6 bohr, "
+                        "spacing 3 bohr), 256 x 256 grid, box 32 bohr, n = 81 + 8 guard, "
+                        f"order {order}, tau = {tau}; no pencil pass (the kinetic factor "
+                        "ends each forward plane pass)",
+            "value": (n + guard) * steps / dt, "unit": "state-steps/s",
+            "ms_per_step": 1e3 * dt / steps, "launch_shapes": tuned,
+            "energies_head": [round(float(x), 8) for x in E[:3]],
+            "fp64_adaptive": {"seconds": round(t_ad, 3), "levels": r["levels"],
+                              "converged": r["converged"],
+                              "max_RH": float(np.max(r["RH"][:n])),
+                              "E_81": float(r["E"][n - 1])}}
+
+
 def batch_throughput(P, torch, steps, warmup, count=64, order=8, tau=0.25, seed=1000):
     """The batched workload: `count` independent random-well problems (grid
     edges from {32, 48, 64, 96}, n ~ U{8..64} states, 4-60 Gaussian wells),
@@ -693,6 +743,10 @@ def main():
     sweep = None
     if not args.no_ttt:
         sweep = order_sweep_small(P)
+    planar_case = None
+    if not args.no_batch:
+        barrier()
+        planar_case = planar_dots(P, torch, args.steps, args.warmup)
 
     # ---- CPU oracle on a bounded sample (rank 0, N = 1 only) -------------------
     cpu = None
@@ -736,6 +790,7 @@ def main():
                        "propagation_ms": prop_ms,
                        "time_to_tol_by_order_ho32": sweep},
             "batch": batch,
+            "planar_quantum_dots": planar_case,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clk,

@@ -242,10 +242,11 @@ def solve_adaptive(Psi0, V, grid, order, tau0, reduce, gamma, n_report, max_step
     each level just above it.  The states kept fixed are the leading ones up to the
     first unconverged state, since a fixed state must precede the propagated
     ones in the Cholesky order of Eq. (4) to stay unchanged.  When the first
-    n_report states have converged (or after max_steps steps), R^H_j is
-    evaluated for the current states: if R^H_j < gamma for all j < n_report
-    the iteration ends; else tau *= reduce and the steps repeat from the
-    current states, all of them propagated again.
+    n_report states have converged (or after max_steps steps), the states are
+    rotated onto the Ritz vectors of their span (the subspace step of Sec.
+    III) and R^H_j is evaluated for them with the Ritz values: if R^H_j <
+    gamma for all j < n_report the iteration ends; else tau *= reduce and
+    the steps repeat from the current states, all of them propagated again.
 
     Returns a dict: E (Ritz values), Psi (Ritz vectors), RH (R^H_j of the
     last basis), levels = [(tau, steps, propagated state-steps), ...] and
@@ -273,6 +274,10 @@ def solve_adaptive(Psi0, V, grid, order, tau0, reduce, gamma, n_report, max_step
             while j < len(RE) and RE[j] < 0.1 * gamma * tau * tau:
                 j += 1
             c += j
+        # R^H of the Ritz vectors: within a nearly degenerate group only the
+        # spanned subspace converges at the rate of the gap to the unwanted
+        # states, and the Ritz vectors of that subspace are its eigenvectors
+        E, Psi, HPsi = energies(Psi, V, grid, ritz=True)
         RH = residual_h(Psi, HPsi, E, grid.dV)
         levels.append((tau, steps, props))
         if np.all(RH[:n_report] < gamma):

@@ -524,23 +524,33 @@ __device__ __forceinline__ void yA(const PlaneGeo<R, NX, NY>& G, C* sm, const C*
 
 // Forward stage B with the global store fused in: column t, block b writes
 // the frequencies ky = b + r2*k1 to the half spectrum.
+// Kinetic factor of frequency (kx, ky) for planar grids (see KinFac).
+template <typename R>
+__device__ __forceinline__ R kin_factor(const KinFac<R>& k, int kx, int ky) {
+  return k.mode == 0 ? k.fx[kx] * k.fy[ky] * k.fz[0] : (k.fx[kx] + k.fy[ky] + k.fz[0]) * k.scale;
+}
+
 template <int R1, typename R, int NX, int NY, typename C>
 __device__ __forceinline__ void yB_fwd_global_r(const PlaneGeo<R, NX, NY>& G, C* sm,
-                                                C* __restrict__ spec) {
+                                                C* __restrict__ spec, const KinFac<R>& kin) {
   constexpr int NT = PlaneGeo<R, NX, NY>::NT;
   for_tasks<NT>(G.nxh, G.ay.r2, [&](int t, int b) {
     C a[R1];
 #pragma unroll
     for (int i = 0; i < R1; ++i) a[i] = sm[G.col(t, i + R1 * b)];
     Dft<R1, -1, C>::run(a);
+    if (kin.fx) {
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) a[k1] = cscale(a[k1], kin_factor(kin, t, b + G.ay.r2 * k1));
+    }
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) spec[(b + G.ay.r2 * k1) * G.nxh + t] = a[k1];
   });
 }
 template <typename R, int NX, int NY, typename C>
 __device__ __forceinline__ void yB_fwd_global(const PlaneGeo<R, NX, NY>& G, C* sm,
-                                              C* __restrict__ spec) {
-  ITP_WITH_RADIX(G.ay.r1, yB_fwd_global_r, G, sm, spec)
+                                              C* __restrict__ spec, const KinFac<R>& kin) {
+  ITP_WITH_RADIX(G.ay.r1, yB_fwd_global_r, G, sm, spec, kin)
 }
 
 // ---- epilogues of the inverse x transform -------------------------------------
@@ -760,7 +770,7 @@ __global__ void __launch_bounds__(launch_threads(PlaneGeo<R, NX, NY>::NT),
   __syncthreads();
   yA<-1>(G, sm, twy);
   __syncthreads();
-  yB_fwd_global(G, sm, static_cast<C*>(a.spec) + spec_off);
+  yB_fwd_global(G, sm, static_cast<C*>(a.spec) + spec_off, a.kin);
 }
 
 // ----------------------------------------------------------------------------
@@ -927,13 +937,18 @@ __global__ void __launch_bounds__(kThreads)
 // slab structure as the pencil pass, along y).
 template <int R1, typename C, int NT>
 __device__ __forceinline__ void col_fwdB_store_r(nt_tag<NT>, const C* sm, C* __restrict__ base,
-                                                 long long rstride, int w, int pw, int r2) {
+                                                 long long rstride, int w, int pw, int r2,
+                                                 const KinFac<decltype(C{}.x)>& kin, int kx0) {
   for_tasks<NT>(pw, r2, [&](int t, int b) {
     if (t >= w) return;
     C v[R1];
 #pragma unroll
     for (int i = 0; i < R1; ++i) v[i] = sm[(i + R1 * b) * pw + t];
     Dft<R1, -1, C>::run(v);
+    if (kin.fx) {
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) v[k1] = cscale(v[k1], kin_factor(kin, kx0 + t, b + r2 * k1));
+    }
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) base[(b + r2 * k1) * rstride + t] = v[k1];
   });
@@ -959,7 +974,8 @@ __device__ __forceinline__ void col_invB_load_r(nt_tag<NT>, C* sm, const C* __re
 
 template <typename R, int NY, int W, int DIR>
 __global__ void __launch_bounds__(launch_threads(task_threads(W)))
-    colpass_kernel(const GridDesc g, void* spec, const void* twy_g, int pw_rt) {
+    colpass_kernel(const GridDesc g, void* spec, const void* twy_g, int pw_rt,
+                   const KinFac<R> kin) {
   constexpr int NT = task_threads(W);
   using C = typename CplxOf<R>::type;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -979,7 +995,7 @@ __global__ void __launch_bounds__(launch_threads(task_threads(W)))
                    ay.r1)
     __syncthreads();
     ITP_WITH_RADIX(ay.r1, col_fwdB_store_r, nt_tag<NT>(), sm, base, (long long)g.nxh, w, pw,
-                   ay.r2)
+                   ay.r2, kin, kx0)
   } else {
     ITP_WITH_RADIX(ay.r1, col_invB_load_r, nt_tag<NT>(), sm, base, twy, (long long)g.nxh, w, pw,
                    ay.r2)
@@ -1204,24 +1220,26 @@ cudaError_t rowpass_launch(const GridDesc& g, const PlaneArgs<R>& a, cudaStream_
 }
 
 template <typename R, int NY, int W, int DIR>
-cudaError_t colpass_one(const GridDesc& g, void* spec, const void* twy, int m, cudaStream_t st) {
+cudaError_t colpass_one(const GridDesc& g, void* spec, const void* twy, int m,
+                        const KinFac<R>& kin, cudaStream_t st) {
   const int cw = g.col_w[sizeof(R) == 4 ? 0 : 1];
   const size_t smem = ((size_t)g.ny * cw + g.ny) * 2 * sizeof(R);
   cudaError_t e = set_smem(colpass_kernel<R, NY, W, DIR>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid((g.nxh + cw - 1) / cw, (unsigned)((long long)m * g.nz));
   colpass_kernel<R, NY, W, DIR><<<grid, launch_threads(task_threads(W)), smem, st>>>(
-      g, spec, twy, cw);
+      g, spec, twy, cw, kin);
   return cudaGetLastError();
 }
 
 template <typename R, int DIR>
-cudaError_t colpass_launch(const GridDesc& g, void* spec, const void* twy, int m, cudaStream_t st) {
+cudaError_t colpass_launch(const GridDesc& g, void* spec, const void* twy, int m,
+                           const KinFac<R>& kin, cudaStream_t st) {
   if (g.ny == 256 && g.col_w[sizeof(R) == 4 ? 0 : 1] == (sizeof(R) == 4 ? 33 : 17)) {
-    if constexpr (sizeof(R) == 4) return colpass_one<R, 256, 33, DIR>(g, spec, twy, m, st);
-    else return colpass_one<R, 256, 17, DIR>(g, spec, twy, m, st);
+    if constexpr (sizeof(R) == 4) return colpass_one<R, 256, 33, DIR>(g, spec, twy, m, kin, st);
+    else return colpass_one<R, 256, 17, DIR>(g, spec, twy, m, kin, st);
   }
-  return colpass_one<R, 0, 0, DIR>(g, spec, twy, m, st);
+  return colpass_one<R, 0, 0, DIR>(g, spec, twy, m, kin, st);
 }
 
 template <typename R>
@@ -1235,7 +1253,7 @@ cudaError_t launch_plane(const GridDesc& g, const PlaneArgs<R>& a, cudaStream_t 
     cudaError_t e = cudaSuccess;
     int n = 0;
     if (a.mode != PLANE_FWD_REAL) {
-      e = colpass_launch<R, 1>(g, a.spec, a.twy, a.m, st);
+      e = colpass_launch<R, 1>(g, a.spec, a.twy, a.m, KinFac<R>{}, st);
       ++n;
       if (e != cudaSuccess) return e;
     }
@@ -1243,7 +1261,7 @@ cudaError_t launch_plane(const GridDesc& g, const PlaneArgs<R>& a, cudaStream_t 
     ++n;
     if (e != cudaSuccess) return e;
     if (a.mode == PLANE_FWD_REAL || a.mode == PLANE_MERGED) {
-      e = colpass_launch<R, -1>(g, a.spec, a.twy, a.m, st);
+      e = colpass_launch<R, -1>(g, a.spec, a.twy, a.m, a.kin, st);
       ++n;
     }
     if (nlaunch) *nlaunch = n;

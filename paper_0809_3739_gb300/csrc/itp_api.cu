@@ -340,6 +340,14 @@ int propagate_lane(itp_handle h, int k, double tau, int s0 = 0, const R* in = nu
     pa.twy = L.twy;
     pa.mode = PLANE_FWD_REAL;
     pa.f_in = L.f_half[i - 1];
+    const bool planar = g.nz == 1;   // the kinetic factor ends each forward pass
+    if (planar) {
+      const R* kt = L.ktab + (i - 1) * tl;
+      pa.kin.fx = kt;
+      pa.kin.fy = kt + g.nxh;
+      pa.kin.fz = kt + g.nxh + g.ny;
+      pa.kin.mode = 0;
+    }
     ITP_LAUNCH(h, ITP_KERNEL_PLANE_FWD, plane_counted<R>(h, pa));
     PencilArgs<R> pe{};
     pe.mode = PENCIL_PROPAGATE;
@@ -351,8 +359,9 @@ int propagate_lane(itp_handle h, int k, double tau, int s0 = 0, const R* in = nu
     pe.scale = (R)1;
     pe.twz = L.twz;
     for (int j = 1; j <= i; ++j) {
-      ITP_LAUNCH(h, pe.mode == PENCIL_PROPAGATE ? ITP_KERNEL_PENCIL : ITP_KERNEL_PENCIL_KINETIC,
-                 launch_pencil<R>(g, pe, h->st));
+      if (!planar)
+        ITP_LAUNCH(h, pe.mode == PENCIL_PROPAGATE ? ITP_KERNEL_PENCIL : ITP_KERNEL_PENCIL_KINETIC,
+                   launch_pencil<R>(g, pe, h->st));
       if (j < i) {
         PlaneArgs<R> pm = pa;
         pm.mode = PLANE_MERGED;
@@ -442,7 +451,16 @@ int energies_lane(itp_handle h, int flags) {
   pa.twy = L.twy;
   pa.mode = PLANE_FWD_REAL;
   pa.f_in = nullptr;
+  const bool planar = g.nz == 1;   // |k|^2/2 ends the forward pass, no pencil pass
+  if (planar) {
+    pa.kin.fx = L.htab;
+    pa.kin.fy = L.htab + g.nxh;
+    pa.kin.fz = L.htab + g.nxh + g.ny;
+    pa.kin.mode = 1;
+    pa.kin.scale = (R)(1.0 / (double)g.n_points);
+  }
   ITP_LAUNCH(h, ITP_KERNEL_PLANE_FWD, plane_counted<R>(h, pa));
+  pa.kin = KinFac<R>{};
   PencilArgs<R> pe{};
   pe.mode = PENCIL_KINETIC;
   pe.m = h->m;
@@ -452,8 +470,9 @@ int energies_lane(itp_handle h, int flags) {
   pe.kz_tab = L.htab + g.nxh + g.ny;
   pe.scale = (R)(1.0 / (double)g.n_points);
   pe.twz = L.twz;
-  ITP_LAUNCH(h, pe.mode == PENCIL_PROPAGATE ? ITP_KERNEL_PENCIL : ITP_KERNEL_PENCIL_KINETIC,
-                 launch_pencil<R>(g, pe, h->st));
+  if (!planar)
+    ITP_LAUNCH(h, pe.mode == PENCIL_PROPAGATE ? ITP_KERNEL_PENCIL : ITP_KERNEL_PENCIL_KINETIC,
+               launch_pencil<R>(g, pe, h->st));
   PlaneArgs<R> ph = pa;
   ph.mode = PLANE_HPSI;
   ph.acc = h->acc;
@@ -800,6 +819,7 @@ int solve_adaptive_lane(itp_handle h, int k, double tau0, double reduce, double 
     long long props = 0;
     while (steps < max_steps && c < n) {
       // fixed leading states enter the orthonormalisation as they are
+      phi = sizeof(R) == 4 ? L.psi_tmp : reinterpret_cast<R*>(h->acc);
       if (c > 0)
         ITP_CUDA(h, cudaMemcpyAsync(phi, L.psi, (size_t)c * row, cudaMemcpyDeviceToDevice,
                                     h->st));
@@ -816,7 +836,12 @@ int solve_adaptive_lane(itp_handle h, int k, double tau0, double reduce, double 
       while (j < m && RE[j] < 0.1 * gamma * tau * tau) ++j;
       c = j;
     }
-    // R^H of the current basis: H psi is where the energies left it
+    // R^H of the Ritz vectors of the current span (within a nearly
+    // degenerate group only the span converges at the rate of the gap to the
+    // unwanted states): rotate, then H psi and the Ritz values again
+    ITP_TRY(energies_lane<R>(h, ITP_RITZ));
+    ITP_TRY(energies_lane<R>(h, 0));
+    phi = sizeof(R) == 4 ? L.psi_tmp : reinterpret_cast<R*>(h->acc);   // the rotation swaps buffers
     ITP_TRY(residual_rows<R>(h, phi, L.psi, 0, 0.0, 0, RH_dev));
     ITP_CUDA(h, cudaMemcpyAsync(RH.data(), RH_dev, (size_t)m * sizeof(double),
                                 cudaMemcpyDeviceToHost, h->st));
@@ -837,9 +862,13 @@ int solve_adaptive_lane(itp_handle h, int k, double tau0, double reduce, double 
   }
   if (levels_out) *levels_out = level;
   if (RH_host) memcpy(RH_host, RH.data(), (size_t)m * sizeof(double));
-  // rotate onto the Ritz vectors and report the Ritz values
+  // the states are the Ritz vectors; report the Ritz values
   h->have_phi = false;
-  return do_energies(h, E_host, ITP_RITZ);
+  ITP_CUDA(h, cudaMemcpyAsync(h->E_host_pinned, h->E_dev, (size_t)m * sizeof(double),
+                              cudaMemcpyDeviceToHost, h->st));
+  ITP_TRY(collect_status(h));
+  if (E_host) memcpy(E_host, h->E_host_pinned, (size_t)m * sizeof(double));
+  return ITP_OK;
 }
 
 // ---- Eq. (sixp): the Romberg-type T_6 (a comparator of Eq. mcomp) ----------------

@@ -36,6 +36,20 @@ enum PencilMode {
   PENCIL_KINETIC = 1,    // * (|k|^2 / 2) / N
 };
 
+// Kinetic factor applied to the half spectrum at the end of a forward plane
+// pass when the grid is planar (nz = 1, no pencil pass): as the pencil pass
+// would, fx[kx] * fy[ky] * fz[0] (mode 0, propagation) or
+// (fx[kx] + fy[ky] + fz[0]) * scale (mode 1, |k|^2/2 for H psi).  fx == null:
+// none.
+template <typename R>
+struct KinFac {
+  const R* fx = nullptr;
+  const R* fy = nullptr;
+  const R* fz = nullptr;
+  int mode = 0;
+  R scale = 0;
+};
+
 // Arguments of one plane pass over `m` states.  R is float or double.
 template <typename R>
 struct PlaneArgs {
@@ -55,6 +69,7 @@ struct PlaneArgs {
   const R* V_r;              // [N] potential in R (PLANE_HPSI with phi_out: output in R)
   const void* twx;           // nx roots (complex R)
   const void* twy;           // ny roots
+  KinFac<R> kin;             // planar grids: kinetic factor after the forward pass
 };
 
 template <typename R>
