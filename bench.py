@@ -89,6 +89,24 @@ NCU_TRAFFIC = {
 }
 
 
+def max_over_ranks(x, device="cuda"):
+    """The largest value of x over all ranks (x itself without a process
+    group): every replica's time is taken as the slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replicas_value(units_per_rank, seconds, world):
+    """Whole-job throughput of `world` independent replicas that each
+    processed units_per_rank units, over the slowest rank's seconds."""
+    return world * units_per_rank / seconds
+
+
 def ncu_traffic(workload, kind):
     import hashlib
     rec = NCU_TRAFFIC.get((workload, kind))
@@ -580,11 +598,8 @@ def main():
     launches = h.kernel_launches - n0
     clk = clocks.stop()
     barrier()
-    dt_t = torch.tensor([dt], device="cuda")
-    if world > 1:
-        dist.all_reduce(dt_t, op=dist.ReduceOp.MAX)
-    dt = float(dt_t.item())
-    value = world * m * args.steps / dt
+    dt = max_over_ranks(dt)
+    value = replicas_value(m * args.steps, dt, world)
 
     # dominant kernel of the step and its roofline
     kinds = {k: v for k, v in prof.items() if v[0] > 0}
@@ -627,8 +642,8 @@ def main():
         h.step_graph(order, tau)
     gend.record(stream)
     gend.synchronize()
-    dt_graph = gstart.elapsed_time(gend) / 1e3
-    graph = {"value": world * m * args.steps / dt_graph, "unit": "state-steps/s",
+    dt_graph = max_over_ranks(gstart.elapsed_time(gend) / 1e3)
+    graph = {"value": replicas_value(m * args.steps, dt_graph, world), "unit": "state-steps/s",
              "ms_per_step": 1e3 * dt_graph / args.steps, "steps": args.steps}
     breakdown = {k: {"launches": v[0], "ms": round(v[1], 3),
                      "share": round(v[1] / total_prof, 4)} for k, v in kinds.items()}
@@ -685,8 +700,8 @@ def main():
             P.itp_energies(h.h, E_host, P.ITP_RITZ_VALUES)
             P.itp.load().itp_get_states(h.h, pin_out.data_ptr())
         barrier()
-        t_e2e = time.perf_counter() - t0
-        e2e = {"value": world * m * K / t_e2e, "unit": "state-steps/s",
+        t_e2e = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": replicas_value(m * K, t_e2e, world), "unit": "state-steps/s",
                "h2d_bytes_per_step": int(psi.nbytes),
                "d2h_bytes_per_step": int(psi.nbytes + E_host.nbytes), "steps": K}
         h.close()
@@ -707,7 +722,8 @@ def main():
         dt64, _ = time_steps(h, stream, order, tau, K, torch)
         prof64 = {k: v for k, v in h.profile_read().items() if v[0] > 0}
         tot64 = sum(v[1] for v in prof64.values())
-        fp64 = {"value": world * m * K / dt64, "unit": "state-steps/s", "steps": K,
+        dt64 = max_over_ranks(dt64)
+        fp64 = {"value": replicas_value(m * K, dt64, world), "unit": "state-steps/s", "steps": K,
                 "ms_per_step": 1e3 * dt64 / K, "launch_shapes": tuned64,
                 "breakdown": {k: {"launches": v[0], "ms": round(v[1], 3),
                                   "share": round(v[1] / tot64, 4)} for k, v in prof64.items()}}
@@ -734,11 +750,10 @@ def main():
     if not args.no_batch:
         barrier()
         batch = batch_throughput(P, torch, args.steps, args.warmup)
-        if world > 1:   # replicas: all ranks' states over the slowest rank's time
-            v = torch.tensor([batch["ms_per_step"]], device="cuda")
-            dist.all_reduce(v, op=dist.ReduceOp.MAX)
-            batch["value"] *= world * batch["ms_per_step"] / float(v.item())
-            batch["ms_per_step"] = float(v.item())
+        slow = max_over_ranks(batch["ms_per_step"])   # replicas: the slowest rank's time
+        batch["value"] = replicas_value(batch["value"] * batch["ms_per_step"] / 1e3, slow / 1e3,
+                                        world)
+        batch["ms_per_step"] = slow
 
     sweep = None
     if not args.no_ttt:
