@@ -692,20 +692,28 @@ def main():
         lib = P.load()
         h.set_states(psi)
         for _ in range(3):
-            h.step(order, tau, ritz="values")
+            h.step_graph(order, tau)
         barrier()
+        phases = {"set_states": 0.0, "step": 0.0, "get_states": 0.0}
         t0 = time.perf_counter()
         for _ in range(K):
-            lib.itp_set_states(h.h, pin_in.data_ptr())
-            h.propagate(order, tau)
-            h.orthonormalize()
-            P.itp_energies(h.h, E_host, P.ITP_RITZ_VALUES)
-            P.itp.load().itp_get_states(h.h, pin_out.data_ptr())
+            ta = time.perf_counter()
+            lib.itp_set_states(h.h, pin_in.data_ptr())     # host -> device, [m][N] FP64
+            tb = time.perf_counter()
+            P.itp_step(h.h, order, tau, P.ITP_RITZ_VALUES, E_host)   # energies -> host
+            tc = time.perf_counter()
+            lib.itp_get_states(h.h, pin_out.data_ptr())    # device -> host, synchronises
+            td = time.perf_counter()
+            phases["set_states"] += tb - ta
+            phases["step"] += tc - tb
+            phases["get_states"] += td - tc
         barrier()
         t_e2e = max_over_ranks(time.perf_counter() - t0)
         e2e = {"value": replicas_value(m * K, t_e2e, world), "unit": "state-steps/s",
                "h2d_bytes_per_step": int(psi.nbytes),
-               "d2h_bytes_per_step": int(psi.nbytes + E_host.nbytes), "steps": K}
+               "d2h_bytes_per_step": int(psi.nbytes + E_host.nbytes), "steps": K,
+               "calls": "itp_set_states (pinned host) + itp_step + itp_get_states (pinned host)",
+               "host_ms_per_step": {k: round(1e3 * v / K, 2) for k, v in phases.items()}}
         h.close()
 
     # ---- the FP64 form of the same workload -----------------------------------
