@@ -362,6 +362,42 @@ def adaptive_to_tol(P, precision, tol=1e-8, order=12, n=120, guard=8):
             "max_abs_error_ha": err, "reached": err < tol}
 
 
+def precision_sweep(P, orders=(4, 8, 12), taus=(0.5, 0.25, 0.125, 0.05), n=20, guard=4):
+    """Accuracy of the mixed form per order and time step: the 3D oscillator
+    on a 64^3 grid in [-8,8)^3, n = 20 (closed shells) + 4 guard states.
+    FP32 steps until the energies change by less than 1e-6 relative (at most
+    400), then FP64 polish steps until they change by less than 1e-11 (at
+    most 60).  Reports the largest |E - (n + 3/2)| over the 20 states after
+    the FP32 phase and after the polish: the FP32 floor, and the time-step
+    bias of the converged Rayleigh-Ritz values, which falls as tau^(4k)."""
+    from itp_workloads import cubic, harmonic_potential, normal_states
+    g = cubic(64, 16.0)
+    V = harmonic_potential(g)
+    E_ref = ho_closed_shells(n)
+    psi = normal_states(n + guard, g.n_points, seed=2024)
+    out = {}
+    for order in orders:
+        for tau in taus:
+            h = P.ItpGrid(64, 64, 64, 16.0, 16.0, 16.0, n, guard, P.ITP_MIXED)
+            h.set_potential(V)
+            h.set_states(psi)
+            E_prev, steps32 = None, 0
+            for steps32 in range(1, 401):
+                E = h.step_graph(order, tau)
+                if E_prev is not None and np.max(np.abs(E[:n] - E_prev[:n])) < 1e-6 * np.max(
+                        np.abs(E[:n])):
+                    break
+                E_prev = E
+            err32 = float(np.max(np.abs(E[:n] - E_ref)))
+            steps64, E = h.polish(order, tau, 1e-11, 60)
+            h.close()
+            out[f"order{order}_tau{tau}"] = {
+                "fp32_steps": steps32, "fp64_steps": steps64,
+                "max_abs_error_fp32_ha": err32,
+                "max_abs_error_polished_ha": float(np.max(np.abs(E[:n] - E_ref)))}
+    return out
+
+
 def order_sweep_small(P, orders=(2, 4, 6, 8, 10, 12), gamma=1e-10):
     """Which order is fastest (the paper found 6 on one Itanium processor):
     the adaptive iteration (tau 0.5, halved between levels, stop on R^H <
@@ -683,7 +719,7 @@ def main():
     if not args.no_e2e:
         K = min(args.steps, 5)
         h = P.ItpGrid(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, w["n_states"], w["n_guard"],
-                      P.ITP_MIXED, cuda_stream=stream.cuda_stream)
+                      P.ITP_MIXED)   # the library's own stream, as a host-side caller has
         h.set_potential(V)
         h.set_tuning(**tuned)
         pin_in = torch.from_numpy(psi).pin_memory()
@@ -716,6 +752,16 @@ def main():
                "d2h_bytes_per_step": int(psi.nbytes + E_host.nbytes), "steps": K,
                "calls": "itp_set_states (pinned host) + itp_step + itp_get_states (pinned host)",
                "host_ms_per_step": {k: round(1e3 * v / K, 2) for k, v in phases.items()}}
+        # the raw copy rate of the same pinned buffers, for comparison
+        dev = torch.empty(pin_in.shape, dtype=pin_in.dtype, device="cuda")
+        dev.copy_(pin_in, non_blocking=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dev.copy_(pin_in, non_blocking=True)
+        pin_out.copy_(dev, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e["raw_copy_gbs_h2d_plus_d2h"] = round(2 * psi.nbytes / (time.perf_counter() - t0) / 1e9, 1)
+        del dev
         h.close()
 
     # ---- the FP64 form of the same workload -----------------------------------
@@ -768,8 +814,10 @@ def main():
         batch["ms_per_step"] = slow
 
     sweep = None
+    prec_sweep = None
     if not args.no_ttt:
         sweep = order_sweep_small(P)
+        prec_sweep = precision_sweep(P)
     planar_case = None
     if not args.no_batch:
         barrier()
@@ -817,7 +865,8 @@ def main():
             "time_to_tol": ttt,
             "orders": {"ms_per_step_by_order": order_cost,
                        "propagation_ms": prop_ms,
-                       "time_to_tol_by_order_ho32": sweep},
+                       "time_to_tol_by_order_ho32": sweep,
+                       "mixed_accuracy_by_order_and_tau_ho64": prec_sweep},
             "batch": batch,
             "planar_quantum_dots": planar_case,
             "e2e": e2e,
