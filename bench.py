@@ -428,6 +428,61 @@ def order_sweep_small(P, orders=(2, 4, 6, 8, 10, 12), gamma=1e-10):
     return out
 
 
+def large_c60(P, torch, steps, warmup, n=120, guard=8, order=8, tau=0.25, seed=1234):
+    """The large workload: C60-like well on a 256^3 grid (16.8 M points), box
+    32 bohr, n = 120 + 8 guard states, order 8, mixed (planes too large for
+    one CTA run as row and column passes).  Graph-replayed steps per second,
+    the row/column passes' achieved GB/s, and the tensor-core Gram's TF32
+    rate.  States from torch's seeded device generator (2.1 G values)."""
+    from itp_workloads import c60_like_potential, cubic
+    g = cubic(256, 32.0)
+    V = c60_like_potential(g)
+    m = n + guard
+    stream = torch.cuda.Stream()
+    h = P.ItpGrid(256, 256, 256, 32.0, 32.0, 32.0, n, guard, P.ITP_MIXED,
+                  cuda_stream=stream.cuda_stream)
+    h.set_potential(V)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    x = torch.randn((m, g.n_points), dtype=torch.float64, device="cuda", generator=gen)
+    torch.cuda.synchronize()
+    P.itp_set_states_device(h.h, x.data_ptr())
+    h.synchronize()
+    del x
+    torch.cuda.empty_cache()
+    for _ in range(warmup):
+        h.step_graph(order, tau)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        E = h.step_graph(order, tau)
+    b.record(stream)
+    b.synchronize()
+    dt = a.elapsed_time(b) / 1e3
+    h.profile(True)
+    h.step(order, tau, ritz="values")
+    prof = {k: v for k, v in h.profile_read().items() if v[0] > 0}
+    h.profile(False)
+    h.close()
+    Nh = g.nz * g.ny * (g.nx // 2 + 1)
+    spec = m * Nh * 8
+    per = {k: {"launches": v[0], "avg_launch_ms": round(v[1] / v[0], 4)} for k, v in prof.items()}
+    # a pencil pass moves the FP32 half spectrum in and out; the overlap
+    # Gram reads the FP32 block and does 3 TF32 products per FP32 product
+    if "pencil" in per:
+        t = per["pencil"]["avg_launch_ms"] / 1e3
+        per["pencil"]["achieved_gbs"] = round(2 * spec / t / 1e9, 1)
+    if "gram" in per:
+        t = per["gram"]["avg_launch_ms"] / 1e3
+        per["gram"]["tf32_tflops"] = round(3 * 2 * 128 * 128 * g.n_points / t / 1e12, 1)
+    return {"workload": f"C60-like well, 256^3 grid, box 32 bohr, n = {n} + {guard} guard, "
+                        f"order {order}, tau = {tau}, mixed (row + column plane passes)",
+            "value": m * steps / dt, "unit": "state-steps/s", "ms_per_step": 1e3 * dt / steps,
+            "steps": steps, "per_kernel": per,
+            "energies_head": [round(float(v), 8) for v in E[:3]]}
+
+
 def planar_dots(P, torch, steps, warmup, order=12, tau=0.25):
     """The paper's planar case: a 9 x 9 array of quantum dots (sech wells,
     depth 2 Ha, width 0.6 bohr, spacing 3 bohr) on a 256 x 256 grid in a
@@ -819,9 +874,12 @@ def main():
         sweep = order_sweep_small(P)
         prec_sweep = precision_sweep(P)
     planar_case = None
+    large = None
     if not args.no_batch:
         barrier()
         planar_case = planar_dots(P, torch, args.steps, args.warmup)
+        barrier()
+        large = large_c60(P, torch, min(args.steps, 5), args.warmup)
 
     # ---- CPU oracle on a bounded sample (rank 0, N = 1 only) -------------------
     cpu = None
@@ -869,6 +927,7 @@ def main():
                        "mixed_accuracy_by_order_and_tau_ho64": prec_sweep},
             "batch": batch,
             "planar_quantum_dots": planar_case,
+            "large_256": large,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clk,
