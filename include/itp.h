@@ -235,10 +235,14 @@ int itp_profile_read(itp_handle h, int kind, long long* launches, double* total_
  *   [ITP_TUNE_PENCIL_W]  kx columns per pencil-pass CTA, 1..nx/2+1 (and the
  *                        FP64 pencil slab, nz*(w+1) complex doubles, within
  *                        one CTA's 227 KB of shared memory)
- *   [ITP_TUNE_SPLIT]     0: one CTA per plane for the x and y transforms
- *                        (only where the plane fits one CTA); 1: row passes
- *                        (x) and column passes (y)
- *   [ITP_TUNE_ROW_TB]    row pairs per row-pass CTA with ITP_TUNE_SPLIT = 1:
+ *   [ITP_TUNE_SPLIT]     plane-pass form: 0: one CTA per plane for the x
+ *                        and y transforms (only where the plane fits one
+ *                        CTA); 1: row passes (x) and column passes (y), three
+ *                        HBM round trips; 2: a cluster of two CTAs per plane
+ *                        exchanging rows through distributed shared memory,
+ *                        one round trip (256 x 256 planes, FP32 lane only)
+ *   [ITP_TUNE_ROW_TB]    row pairs per row-pass CTA with ITP_TUNE_SPLIT = 1
+ *                        (0 otherwise):
  *                        8, 16, or 32 (32: FP32 with nx = 256 only); it
  *                        divides ny/2
  *   [ITP_TUNE_GRAM]      CTAs (partial sums) of the overlap kernel,

@@ -28,8 +28,12 @@
 // Kernels are specialised at compile time for the common edge lengths
 // (all index arithmetic folds to constants); a generic instantiation takes
 // the sizes at run time.
+#include <cooperative_groups.h>
+
 #include "fft_common.cuh"
 #include "itp_kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace itp {
 
@@ -140,14 +144,16 @@ __device__ __forceinline__ float2 cmulri<float2>(float2 a, float2 f) {
 
 // ----------------------------------------------------------------------------
 // Shared-memory geometry of one plane.
-template <typename R, int NX, int NY>
+template <typename R, int NX, int NY, int NTT>
 struct PlaneGeo {
   using C = typename CplxOf<R>::type;
-  static constexpr int NT = kThreads;
+  static constexpr int NT = NTT;
   AxisT<NX> ax;
   AxisT<NY> ay;
   int nx, ny, nxh, npair, pp;
   int gpair;   // row-pair stride of the global (transposed) real layout
+  int srs;     // row stride of the global half spectrum (complex)
+  int kym, kya;  // local spectrum row j holds ky = kym * j + kya
   __device__ __forceinline__ PlaneGeo(const GridDesc& g)
       : ax(g.nx, g.rx1, g.rx2), ay(g.ny, g.ry1, g.ry2) {
     nx = NX ? NX : g.nx;
@@ -156,6 +162,9 @@ struct PlaneGeo {
     npair = ny / 2;
     gpair = npair;
     pp = NX ? row_pitch(NX) : g.pp;
+    srs = nxh;
+    kym = 1;
+    kya = 0;
   }
   // x rows: transform t = row pair, element e = x (padded)
   __device__ __forceinline__ int row(int t, int e) const { return t * pp + swz(e); }
@@ -169,11 +178,11 @@ struct PlaneGeo {
 // Forward stage A with the global load fused in: element x of row pair t is
 // the pair (psi[y=2t][x], psi[y=2t+1][x]) = src[x * npair + t] (transposed
 // layout), times the factor pair f[x * npair + t].
-template <int R2, typename R, int NX, int NY, typename C>
-__device__ __forceinline__ void xA_fwd_global_r(const PlaneGeo<R, NX, NY>& G, C* sm,
+template <int R2, typename R, int NX, int NY, int NTT, typename C>
+__device__ __forceinline__ void xA_fwd_global_r(const PlaneGeo<R, NX, NY, NTT>& G, C* sm,
                                                 const C* __restrict__ src,
                                                 const C* __restrict__ f, const C* tw) {
-  constexpr int NT = PlaneGeo<R, NX, NY>::NT;
+  constexpr int NT = PlaneGeo<R, NX, NY, NTT>::NT;
   for_tasks<NT>(G.npair, G.ax.r1, [&](int t, int n1) {
     C a[R2];
 #pragma unroll
@@ -191,17 +200,17 @@ __device__ __forceinline__ void xA_fwd_global_r(const PlaneGeo<R, NX, NY>& G, C*
     for (int j = 0; j < R2; ++j) sm[G.row(t, n1 + G.ax.r1 * j)] = a[j];
   });
 }
-template <typename R, int NX, int NY, typename C>
-__device__ __forceinline__ void xA_fwd_global(const PlaneGeo<R, NX, NY>& G, C* sm,
+template <typename R, int NX, int NY, int NTT, typename C>
+__device__ __forceinline__ void xA_fwd_global(const PlaneGeo<R, NX, NY, NTT>& G, C* sm,
                                               const C* __restrict__ src,
                                               const C* __restrict__ f, const C* tw) {
   ITP_WITH_RADIX(G.ax.r2, xA_fwd_global_r, G, sm, src, f, tw)
 }
 
 // Stage B (DIR = -1 forward, +1 inverse with the conjugate twiddle after).
-template <int R1, int DIR, typename R, int NX, int NY, typename C>
-__device__ __forceinline__ void xB_r(const PlaneGeo<R, NX, NY>& G, C* sm, const C* tw) {
-  constexpr int NT = PlaneGeo<R, NX, NY>::NT;
+template <int R1, int DIR, typename R, int NX, int NY, int NTT, typename C>
+__device__ __forceinline__ void xB_r(const PlaneGeo<R, NX, NY, NTT>& G, C* sm, const C* tw) {
+  constexpr int NT = PlaneGeo<R, NX, NY, NTT>::NT;
   for_tasks<NT>(G.npair, G.ax.r2, [&](int t, int b) {
     C a[R1];
 #pragma unroll
@@ -219,8 +228,8 @@ template <int R1, typename G_, typename C>
 __device__ __forceinline__ void xB_fwd_r(const G_& G, C* sm, const C* tw) { xB_r<R1, -1>(G, sm, tw); }
 template <int R1, typename G_, typename C>
 __device__ __forceinline__ void xB_inv_r(const G_& G, C* sm, const C* tw) { xB_r<R1, 1>(G, sm, tw); }
-template <int DIR, typename R, int NX, int NY, typename C>
-__device__ __forceinline__ void xB(const PlaneGeo<R, NX, NY>& G, C* sm, const C* tw) {
+template <int DIR, typename R, int NX, int NY, int NTT, typename C>
+__device__ __forceinline__ void xB(const PlaneGeo<R, NX, NY, NTT>& G, C* sm, const C* tw) {
   if (G.ax.r1 == 1) return;
   if (DIR < 0) {
     ITP_WITH_RADIX(G.ax.r1, xB_fwd_r, G, sm, tw)
@@ -233,10 +242,10 @@ __device__ __forceinline__ void xB(const PlaneGeo<R, NX, NY>& G, C* sm, const C*
 // epi.apply<R2>(t, n1, a) receives a[j] = element x = n1 + r1*j of row pair
 // t and either stores it somewhere (returns false) or transforms it and asks
 // for the forward stage A to follow in registers (returns true).
-template <int R2, typename R, int NX, int NY, typename C, typename Epi>
-__device__ __forceinline__ void xA_inv_then_r(const PlaneGeo<R, NX, NY>& G, C* sm, const C* tw,
+template <int R2, typename R, int NX, int NY, int NTT, typename C, typename Epi>
+__device__ __forceinline__ void xA_inv_then_r(const PlaneGeo<R, NX, NY, NTT>& G, C* sm, const C* tw,
                                               const Epi& epi) {
-  constexpr int NT = PlaneGeo<R, NX, NY>::NT;
+  constexpr int NT = PlaneGeo<R, NX, NY, NTT>::NT;
   for_tasks<NT>(G.npair, G.ax.r1, [&](int t, int n1) {
     C a[R2];
 #pragma unroll
@@ -253,8 +262,8 @@ __device__ __forceinline__ void xA_inv_then_r(const PlaneGeo<R, NX, NY>& G, C* s
     }
   });
 }
-template <typename R, int NX, int NY, typename C, typename Epi>
-__device__ __forceinline__ void xA_inv_then(const PlaneGeo<R, NX, NY>& G, C* sm, const C* tw,
+template <typename R, int NX, int NY, int NTT, typename C, typename Epi>
+__device__ __forceinline__ void xA_inv_then(const PlaneGeo<R, NX, NY, NTT>& G, C* sm, const C* tw,
                                             const Epi& epi) {
   ITP_WITH_RADIX(G.ax.r2, xA_inv_then_r, G, sm, tw, epi)
 }
@@ -262,11 +271,11 @@ __device__ __forceinline__ void xA_inv_then(const PlaneGeo<R, NX, NY>& G, C* sm,
 // Real transform along x, forward: split the spectrum Z of each packed row
 // (a + i b) into A = FFT(a), B = FFT(b), k = 0..nx/2.  One warp per row
 // pair; Z is read in digit-swapped order.
-template <typename R, int NX, int NY>
-__device__ __forceinline__ void x_split(const PlaneGeo<R, NX, NY>& G, typename CplxOf<R>::type* sm) {
+template <typename R, int NX, int NY, int NTT>
+__device__ __forceinline__ void x_split(const PlaneGeo<R, NX, NY, NTT>& G, typename CplxOf<R>::type* sm) {
   using C = typename CplxOf<R>::type;
   constexpr int MAXQ = NX ? (NX / 2 + 32) / 32 : 5;
-  constexpr int NW = PlaneGeo<R, NX, NY>::NT / 32;
+  constexpr int NW = PlaneGeo<R, NX, NY, NTT>::NT / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int half = G.nx >> 1;
   const Axis ax{G.ax.L, G.ax.r1, G.ax.r2};
@@ -303,11 +312,11 @@ __device__ __forceinline__ void x_split(const PlaneGeo<R, NX, NY>& G, typename C
 // Inverse of x_split (Hermitian extension; the imaginary parts of the
 // self-conjugate bins k = 0, nx/2 are dropped, as a complex-to-real
 // transform does), writing Z in digit-swapped order.
-template <typename R, int NX, int NY>
-__device__ __forceinline__ void x_merge(const PlaneGeo<R, NX, NY>& G, typename CplxOf<R>::type* sm) {
+template <typename R, int NX, int NY, int NTT>
+__device__ __forceinline__ void x_merge(const PlaneGeo<R, NX, NY, NTT>& G, typename CplxOf<R>::type* sm) {
   using C = typename CplxOf<R>::type;
   constexpr int MAXQ = NX ? (NX / 2 + 32) / 32 : 5;
-  constexpr int NW = PlaneGeo<R, NX, NY>::NT / 32;
+  constexpr int NW = PlaneGeo<R, NX, NY, NTT>::NT / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int half = G.nx >> 1;
   const Axis ax{G.ax.L, G.ax.r1, G.ax.r2};
@@ -351,9 +360,9 @@ __device__ __forceinline__ void x_merge(const PlaneGeo<R, NX, NY>& G, typename C
 // frequencies k = b + r2*k1 (k1 < r1) of its row, which are exactly the
 // outputs of its forward stage-B task; the partner frequencies nx - k sit in
 // lane (r2 - b) % r2 of the same group and arrive by warp shuffles.
-template <int R1, typename R, int NX, int NY, typename C>
-__device__ __forceinline__ void xB_fwd_split_r(const PlaneGeo<R, NX, NY>& G, C* sm) {
-  constexpr int NW = PlaneGeo<R, NX, NY>::NT / 32;
+template <int R1, typename R, int NX, int NY, int NTT, typename C>
+__device__ __forceinline__ void xB_fwd_split_r(const PlaneGeo<R, NX, NY, NTT>& G, C* sm) {
+  constexpr int NW = PlaneGeo<R, NX, NY, NTT>::NT / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (warp >= NW) return;
   const int r2 = G.ax.r2, rpw = 32 / r2;
@@ -401,9 +410,9 @@ __device__ __forceinline__ void xB_fwd_split_r(const PlaneGeo<R, NX, NY>& G, C* 
 // Inverse: each lane builds its stage-B' inputs Z[b + r2*a] (a < r1) from
 // the half-spectrum rows A, B (Hermitian extension, imaginary parts of the
 // self-conjugate bins dropped), the row's lanes synchronise, then stage B'.
-template <int R1, typename R, int NX, int NY, typename C>
-__device__ __forceinline__ void xB_inv_merge_r(const PlaneGeo<R, NX, NY>& G, C* sm, const C* tw) {
-  constexpr int NW = PlaneGeo<R, NX, NY>::NT / 32;
+template <int R1, typename R, int NX, int NY, int NTT, typename C>
+__device__ __forceinline__ void xB_inv_merge_r(const PlaneGeo<R, NX, NY, NTT>& G, C* sm, const C* tw) {
+  constexpr int NW = PlaneGeo<R, NX, NY, NTT>::NT / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (warp >= NW) return;
   const int r2 = G.ax.r2, rpw = 32 / r2;
@@ -447,16 +456,16 @@ __device__ __forceinline__ void xB_inv_merge_r(const PlaneGeo<R, NX, NY>& G, C* 
   }
 }
 
-template <typename R, int NX, int NY, typename C>
-__device__ __forceinline__ void xB_fwd_split(const PlaneGeo<R, NX, NY>& G, C* sm, const C* tw) {
+template <typename R, int NX, int NY, int NTT, typename C>
+__device__ __forceinline__ void xB_fwd_split(const PlaneGeo<R, NX, NY, NTT>& G, C* sm, const C* tw) {
   if (G.ax.r1 == 1 || G.ax.r2 > 32) {   // single-stage rows: split on its own
     x_split(G, sm);
     return;
   }
   ITP_WITH_RADIX(G.ax.r1, xB_fwd_split_r, G, sm)
 }
-template <typename R, int NX, int NY, typename C>
-__device__ __forceinline__ void xB_inv_merge(const PlaneGeo<R, NX, NY>& G, C* sm, const C* tw) {
+template <typename R, int NX, int NY, int NTT, typename C>
+__device__ __forceinline__ void xB_inv_merge(const PlaneGeo<R, NX, NY, NTT>& G, C* sm, const C* tw) {
   if (G.ax.r1 == 1 || G.ax.r2 > 32) {
     x_merge(G, sm);
     __syncthreads();
@@ -469,14 +478,14 @@ __device__ __forceinline__ void xB_inv_merge(const PlaneGeo<R, NX, NY>& G, C* sm
 // ---- y stages (columns) -------------------------------------------------------
 // Inverse stage B' with the global load fused in: column t, block b reads
 // the frequencies ky = b + r2*a (a < r1) straight from the half spectrum.
-template <int R1, typename R, int NX, int NY, typename C>
-__device__ __forceinline__ void yB_inv_global_r(const PlaneGeo<R, NX, NY>& G, C* sm,
+template <int R1, typename R, int NX, int NY, int NTT, typename C>
+__device__ __forceinline__ void yB_inv_global_r(const PlaneGeo<R, NX, NY, NTT>& G, C* sm,
                                                 const C* __restrict__ spec, const C* tw) {
-  constexpr int NT = PlaneGeo<R, NX, NY>::NT;
+  constexpr int NT = PlaneGeo<R, NX, NY, NTT>::NT;
   for_tasks<NT>(G.nxh, G.ay.r2, [&](int t, int b) {
     C a[R1];
 #pragma unroll
-    for (int i = 0; i < R1; ++i) a[i] = spec[(b + G.ay.r2 * i) * G.nxh + t];
+    for (int i = 0; i < R1; ++i) a[i] = spec[(b + G.ay.r2 * i) * G.srs + t];
     Dft<R1, 1, C>::run(a);
     if (R1 > 1) {
 #pragma unroll
@@ -486,16 +495,16 @@ __device__ __forceinline__ void yB_inv_global_r(const PlaneGeo<R, NX, NY>& G, C*
     for (int i = 0; i < R1; ++i) sm[G.col(t, i + R1 * b)] = a[i];
   });
 }
-template <typename R, int NX, int NY, typename C>
-__device__ __forceinline__ void yB_inv_global(const PlaneGeo<R, NX, NY>& G, C* sm,
+template <typename R, int NX, int NY, int NTT, typename C>
+__device__ __forceinline__ void yB_inv_global(const PlaneGeo<R, NX, NY, NTT>& G, C* sm,
                                               const C* __restrict__ spec, const C* tw) {
   ITP_WITH_RADIX(G.ay.r1, yB_inv_global_r, G, sm, spec, tw)
 }
 
 // Stage A on columns (DIR = -1 forward with twiddle after; +1 inverse).
-template <int R2, int DIR, typename R, int NX, int NY, typename C>
-__device__ __forceinline__ void yA_r(const PlaneGeo<R, NX, NY>& G, C* sm, const C* tw) {
-  constexpr int NT = PlaneGeo<R, NX, NY>::NT;
+template <int R2, int DIR, typename R, int NX, int NY, int NTT, typename C>
+__device__ __forceinline__ void yA_r(const PlaneGeo<R, NX, NY, NTT>& G, C* sm, const C* tw) {
+  constexpr int NT = PlaneGeo<R, NX, NY, NTT>::NT;
   for_tasks<NT>(G.nxh, G.ay.r1, [&](int t, int n1) {
     C a[R2];
 #pragma unroll
@@ -513,8 +522,8 @@ template <int R2, typename G_, typename C>
 __device__ __forceinline__ void yA_fwd_r(const G_& G, C* sm, const C* tw) { yA_r<R2, -1>(G, sm, tw); }
 template <int R2, typename G_, typename C>
 __device__ __forceinline__ void yA_inv_r(const G_& G, C* sm, const C* tw) { yA_r<R2, 1>(G, sm, tw); }
-template <int DIR, typename R, int NX, int NY, typename C>
-__device__ __forceinline__ void yA(const PlaneGeo<R, NX, NY>& G, C* sm, const C* tw) {
+template <int DIR, typename R, int NX, int NY, int NTT, typename C>
+__device__ __forceinline__ void yA(const PlaneGeo<R, NX, NY, NTT>& G, C* sm, const C* tw) {
   if (DIR < 0) {
     ITP_WITH_RADIX(G.ay.r2, yA_fwd_r, G, sm, tw)
   } else {
@@ -530,10 +539,10 @@ __device__ __forceinline__ R kin_factor(const KinFac<R>& k, int kx, int ky) {
   return k.mode == 0 ? k.fx[kx] * k.fy[ky] * k.fz[0] : (k.fx[kx] + k.fy[ky] + k.fz[0]) * k.scale;
 }
 
-template <int R1, typename R, int NX, int NY, typename C>
-__device__ __forceinline__ void yB_fwd_global_r(const PlaneGeo<R, NX, NY>& G, C* sm,
+template <int R1, typename R, int NX, int NY, int NTT, typename C>
+__device__ __forceinline__ void yB_fwd_global_r(const PlaneGeo<R, NX, NY, NTT>& G, C* sm,
                                                 C* __restrict__ spec, const KinFac<R>& kin) {
-  constexpr int NT = PlaneGeo<R, NX, NY>::NT;
+  constexpr int NT = PlaneGeo<R, NX, NY, NTT>::NT;
   for_tasks<NT>(G.nxh, G.ay.r2, [&](int t, int b) {
     C a[R1];
 #pragma unroll
@@ -541,14 +550,14 @@ __device__ __forceinline__ void yB_fwd_global_r(const PlaneGeo<R, NX, NY>& G, C*
     Dft<R1, -1, C>::run(a);
     if (kin.fx) {
 #pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) a[k1] = cscale(a[k1], kin_factor(kin, t, b + G.ay.r2 * k1));
+      for (int k1 = 0; k1 < R1; ++k1) a[k1] = cscale(a[k1], kin_factor(kin, t, (b + G.ay.r2 * k1) * G.kym + G.kya));
     }
 #pragma unroll
-    for (int k1 = 0; k1 < R1; ++k1) spec[(b + G.ay.r2 * k1) * G.nxh + t] = a[k1];
+    for (int k1 = 0; k1 < R1; ++k1) spec[(b + G.ay.r2 * k1) * G.srs + t] = a[k1];
   });
 }
-template <typename R, int NX, int NY, typename C>
-__device__ __forceinline__ void yB_fwd_global(const PlaneGeo<R, NX, NY>& G, C* sm,
+template <typename R, int NX, int NY, int NTT, typename C>
+__device__ __forceinline__ void yB_fwd_global(const PlaneGeo<R, NX, NY, NTT>& G, C* sm,
                                               C* __restrict__ spec, const KinFac<R>& kin) {
   ITP_WITH_RADIX(G.ay.r1, yB_fwd_global_r, G, sm, spec, kin)
 }
@@ -705,13 +714,14 @@ struct EpiHpsi {
 };
 
 template <typename R, int NX, int NY, int MODE>
-__global__ void __launch_bounds__(launch_threads(PlaneGeo<R, NX, NY>::NT),
+__global__ void __launch_bounds__(launch_threads(kThreads),
                                   min_blocks(plane_smem_ct(NX, NY, sizeof(R)),
                                              sizeof(R) == 4 ? 3 : 2))
     plane_kernel(const GridDesc g, const PlaneArgs<R> a) {
   using C = typename CplxOf<R>::type;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const PlaneGeo<R, NX, NY> G(g);
+  constexpr int NTT = kThreads;
+  const PlaneGeo<R, NX, NY, NTT> G(g);
   C* sm = reinterpret_cast<C*>(smraw);
   C* twx = sm + G.npair * G.pp;   // nx roots
   C* twy = twx + G.nx;            // ny roots
@@ -846,14 +856,153 @@ __device__ __forceinline__ void pencil_invA_r(nt_tag<NT>, const C* sm, C* __rest
 }
 
 // ----------------------------------------------------------------------------
+// 256 x 256 FP32 planes on a cluster of two CTAs (one HBM round trip per pass
+// where the row + column passes below take three).  CTA r of the pair holds
+// the real-space rows y = 128 r + n (n < 128) and the half-spectrum rows
+// ky = 2 j + r (j < 128), each in the one-CTA layout with 64 row pairs.  The
+// length-256 y transform is a radix-2 step across the pair plus local
+// 128-point transforms:
+//   forward  (decimation in frequency): X(2j)   = FFT128[x(n) + x(n+128)](j),
+//                                       X(2j+1) = FFT128[(x(n) - x(n+128)) w^n](j);
+//   inverse  (decimation in time):      x(n)     = E(n) + w^-n O(n),
+//                                       x(n+128) = E(n) - w^-n O(n),
+// E, O the inverse 128-point transforms of the even and odd rows, w = exp(-2 pi i/256).
+// The radix-2 step reads the partner CTA's shared memory (distributed shared
+// memory) in two halves: read the partner's values, cluster barrier, write
+// the own values.
+constexpr int kC2Threads = 512;
+
+template <int DIR, typename G_>
+__device__ __forceinline__ void c2_exchange(const G_& G, float2* sm, const float2* tw2,
+                                            cg::cluster_group& cl, int rank) {
+  constexpr int NT = G_::NT;
+  const float2* psm = cl.map_shared_rank(sm, rank ^ 1);
+  const int total = 128 * G.nxh;   // (n, t): 128 rows, nxh columns
+  const int halfcnt = (total + 1) / 2;
+  constexpr int MAXQ = (128 * 129 / 2 + 1 + NT - 1) / NT;
+  cl.sync();   // the partner's local stage is complete
+  for (int h = 0; h < 2; ++h) {
+    const int e0 = h * halfcnt, e1 = min(total, e0 + halfcnt);
+    float2 pv[MAXQ];
+#pragma unroll
+    for (int q = 0; q < MAXQ; ++q) {
+      const int e = e0 + (int)threadIdx.x + NT * q;
+      if (e < e1) {
+        const int n = e / G.nxh, t = e - n * G.nxh;
+        pv[q] = psm[G.col(t, n)];
+      }
+    }
+    cl.sync();   // every remote read of this half is done before it is overwritten
+#pragma unroll
+    for (int q = 0; q < MAXQ; ++q) {
+      const int e = e0 + (int)threadIdx.x + NT * q;
+      if (e < e1) {
+        const int n = e / G.nxh, t = e - n * G.nxh;
+        const int pos = G.col(t, n);
+        const float2 own = sm[pos];
+        float2 r;
+        if (DIR < 0) {   // forward: rank 0 x0 + x1, rank 1 (x0 - x1) w^n
+          r = rank == 0 ? cadd(own, pv[q]) : cmul(csub(pv[q], own), tw2[n]);
+        } else {         // inverse: rank 0 E + w^-n O, rank 1 E - w^-n O
+          r = rank == 0 ? cadd(own, cmulc(pv[q], tw2[n])) : csub(pv[q], cmulc(own, tw2[n]));
+        }
+        sm[pos] = r;
+      }
+    }
+  }
+}
+
+template <int MODE>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kC2Threads, 1)
+    plane_c2_kernel(const GridDesc g, const PlaneArgs<float> a) {
+  using R = float;
+  using C = float2;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  PlaneGeo<R, 256, 128, kC2Threads> G(g);
+  G.gpair = 128;          // row pairs of the whole plane (global real layout)
+  G.srs = 2 * G.nxh;      // this CTA's spectrum rows ky = 2 j + rank
+  G.kym = 2;
+  G.kya = rank;
+  C* sm = reinterpret_cast<C*>(smraw);
+  C* twx = sm + G.npair * G.pp;   // 256 roots
+  C* twy = twx + 256;             // 128 roots of the local transforms: w^(2j)
+  C* tw2 = twy + 128;             // w^n, n < 128, of the radix-2 step
+  const C* tg = static_cast<const C*>(a.twy);
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) twx[i] = static_cast<const C*>(a.twx)[i];
+  for (int i = threadIdx.x; i < 128; i += blockDim.x) {
+    twy[i] = tg[2 * i];
+    tw2[i] = tg[i];
+  }
+  const int z = blockIdx.x >> 1, s = blockIdx.y;
+  const long long plane_pts = 256LL * 256;
+  const long long real_off = (long long)s * g.n_points + (long long)z * plane_pts;
+  const long long spec_off = ((long long)s * g.nz + z) * 256LL * G.nxh;
+  const long long fac_off = (long long)z * plane_pts;
+  const int t0 = 64 * rank;   // first (global) row pair of this CTA
+  __syncthreads();
+
+  if constexpr (MODE == PLANE_FWD_REAL) {
+    const C* src = reinterpret_cast<const C*>(a.in_real + real_off) + t0;
+    const C* f = a.f_in ? reinterpret_cast<const C*>(a.f_in + fac_off) + t0 : nullptr;
+    xA_fwd_global(G, sm, src, f, twx);
+    __syncthreads();
+  } else {
+    yB_inv_global(G, sm, static_cast<const C*>(a.spec) + spec_off + rank * G.nxh, twy);
+    __syncthreads();
+    yA<1>(G, sm, twy);
+    __syncthreads();
+    c2_exchange<1>(G, sm, tw2, cl, rank);
+    __syncthreads();
+    xB_inv_merge(G, sm, twx);
+    __syncthreads();
+    if constexpr (MODE == PLANE_MERGED) {
+      EpiMerged<R> epi{reinterpret_cast<const C*>(a.f_mid + fac_off) + t0, G.gpair, G.ax.r1};
+      xA_inv_then(G, sm, twx, epi);
+      __syncthreads();
+    } else if constexpr (MODE == PLANE_TERM) {
+      EpiTerm<R> epi{reinterpret_cast<const C*>(a.f_out + fac_off) + t0,
+                     static_cast<C*>(a.spec) + spec_off + t0, (R)a.coef, G.gpair, G.ax.r1};
+      xA_inv_then(G, sm, twx, epi);
+      return;
+    } else if constexpr (MODE == PLANE_COMBINE) {
+      EpiCombinePair<R> epi{reinterpret_cast<const C*>(a.f_out + fac_off) + t0,
+                            reinterpret_cast<float4*>(a.acc + real_off) + t0,
+                            a.phi_out ? reinterpret_cast<C*>(a.phi_out + real_off) + t0 : nullptr,
+                            (float)a.coef, a.acc_init, G.gpair, G.ax.r1};
+      xA_inv_then(G, sm, twx, epi);
+      return;
+    } else if constexpr (MODE == PLANE_HPSI) {
+      EpiHpsi<R> epi{reinterpret_cast<const C*>(a.in_real + real_off) + t0,
+                     reinterpret_cast<const double2*>(a.V + fac_off) + t0,
+                     reinterpret_cast<double2*>(a.acc + real_off) + t0,
+                     reinterpret_cast<const C*>(a.V_r + fac_off) + t0,
+                     reinterpret_cast<C*>(a.phi_out + real_off) + t0, G.gpair, G.ax.r1};
+      xA_inv_then(G, sm, twx, epi);
+      return;
+    } else {
+      return;
+    }
+  }
+  xB_fwd_split(G, sm, twx);
+  __syncthreads();
+  c2_exchange<-1>(G, sm, tw2, cl, rank);
+  __syncthreads();
+  yA<-1>(G, sm, twy);
+  __syncthreads();
+  yB_fwd_global(G, sm, static_cast<C*>(a.spec) + spec_off + rank * G.nxh, a.kin);
+}
+
+// ----------------------------------------------------------------------------
 // Split plane passes, for planes whose half spectrum does not fit one CTA's
 // shared memory (nx = ny = 256 in FP32, >= 192 in FP64).  A row pass does
 // the x transform (and the mode's point-wise epilogue) of a block of TB row
 // pairs; column passes do the y transform.  Between them the data is kept
 // in the half-spectrum layout [z][y][kx] with y not yet transformed.
 template <typename R, int NX, int TB>
-struct RowGeo : PlaneGeo<R, NX, 2 * TB> {
-  __device__ __forceinline__ RowGeo(const GridDesc& g) : PlaneGeo<R, NX, 2 * TB>(g) {
+struct RowGeo : PlaneGeo<R, NX, 2 * TB, kThreads> {
+  __device__ __forceinline__ RowGeo(const GridDesc& g) : PlaneGeo<R, NX, 2 * TB, kThreads>(g) {
     this->ny = 2 * TB;
     this->npair = TB;
     this->gpair = g.ny / 2;
@@ -1248,6 +1397,34 @@ cudaError_t launch_plane(const GridDesc& g, const PlaneArgs<R>& a, cudaStream_t 
   // FP32 H psi passes write FP32 (potential and output in R)
   if (a.mode == PLANE_HPSI && sizeof(R) == 4 && (!a.V_r || !a.phi_out))
     return cudaErrorInvalidValue;
+  if (g.split_planes[sizeof(R) == 4 ? 0 : 1] == 2) {
+    // 256 x 256 FP32 planes on two-CTA clusters
+    if constexpr (sizeof(R) == 4) {
+      if (g.nx != 256 || g.ny != 256) return cudaErrorInvalidValue;
+      const size_t smem = ((size_t)64 * row_pitch(256) + 512) * sizeof(float2);
+      dim3 grid(2 * g.nz, a.m);
+      cudaError_t e;
+      switch (a.mode) {
+#define ITP_C2_CASE(M)                                                      \
+  case M:                                                                   \
+    e = set_smem(plane_c2_kernel<M>, smem);                                 \
+    if (e != cudaSuccess) return e;                                         \
+    plane_c2_kernel<M><<<grid, kC2Threads, smem, st>>>(g, a);               \
+    break;
+        ITP_C2_CASE(PLANE_FWD_REAL)
+        ITP_C2_CASE(PLANE_MERGED)
+        ITP_C2_CASE(PLANE_COMBINE)
+        ITP_C2_CASE(PLANE_HPSI)
+        ITP_C2_CASE(PLANE_TERM)
+#undef ITP_C2_CASE
+        default:
+          return cudaErrorInvalidValue;
+      }
+      return cudaGetLastError();
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  }
   if (g.split_planes[sizeof(R) == 4 ? 0 : 1]) {
     // planes too large for one CTA: column passes for y, row passes for x
     cudaError_t e = cudaSuccess;

@@ -312,7 +312,7 @@ int propagate_lane(itp_handle h, int k, double tau, int s0 = 0, const R* in = nu
   ITP_TRY(prepare_tables<R>(h, L, k, tau));
   const GridDesc& g = h->g;
   const size_t tl = (size_t)g.nxh + g.ny + g.nz;
-  bool fused = sizeof(R) == 4 && L.fused_ok && !g.split_planes[0];
+  bool fused = sizeof(R) == 4 && L.fused_ok && g.split_planes[0] != 1;
   if (fused) {
     L.work_terms[0] = L.work;
     for (int i = 1; i < k && fused; ++i) {
@@ -596,7 +596,7 @@ template <typename R>
 int step_resources(itp_handle h, int k, double tau) {
   Lane<R>& L = lane_of<R>(h);
   ITP_TRY(prepare_tables<R>(h, L, k, tau));
-  if (sizeof(R) == 4 && L.fused_ok && !h->g.split_planes[0]) {
+  if (sizeof(R) == 4 && L.fused_ok && h->g.split_planes[0] != 1) {
     L.work_terms[0] = L.work;
     for (int i = 1; i < k; ++i) {
       if (!L.work_terms[i] &&
@@ -632,13 +632,15 @@ int set_tuning(itp_handle h, const int* t) {
             chunks = t[ITP_TUNE_GRAM];
   if (w < 1 || w > g.nxh || ((size_t)g.nz * w + g.nz) * 16 > kSmemLimit)
     return fail(h, ITP_ERR_ARG, "pencil width %d not in 1..%d or too large", w, g.nxh);
-  if (split != 0 && split != 1) return fail(h, ITP_ERR_ARG, "split must be 0 or 1");
+  if (split < 0 || split > 2) return fail(h, ITP_ERR_ARG, "plane form must be 0, 1 or 2");
   if (!split && plane_smem_bytes(g, rb) > kSmemLimit)
     return fail(h, ITP_ERR_ARG, "a %dx%d plane does not fit one CTA", g.nx, g.ny);
-  if (split && !(tb == 8 || tb == 16 || tb == 32) )
+  if (split == 2 && !(pi == 0 && g.nx == 256 && g.ny == 256))
+    return fail(h, ITP_ERR_ARG, "two-CTA cluster planes are 256x256 FP32 only");
+  if (split == 1 && !(tb == 8 || tb == 16 || tb == 32) )
     return fail(h, ITP_ERR_ARG, "row-pass block %d not 8, 16 or 32", tb);
-  if (split && ((g.ny / 2) % tb != 0 || ((size_t)tb * g.pp + g.nx) * 2 * rb > 96 * 1024 ||
-                (tb == 32 && !(pi == 0 && g.nx == 256))))
+  if (split == 1 && ((g.ny / 2) % tb != 0 || ((size_t)tb * g.pp + g.nx) * 2 * rb > 96 * 1024 ||
+                     (tb == 32 && !(pi == 0 && g.nx == 256))))
     return fail(h, ITP_ERR_ARG, "row-pass block %d does not suit a %dx%d plane", tb, g.nx, g.ny);
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -647,8 +649,8 @@ int set_tuning(itp_handle h, const int* t) {
   g.pencil_w = w;
   g.pencil_pitch = w;
   g.split_planes[pi] = split;
-  g.row_tb[pi] = split ? tb : 0;
-  if (split) {
+  g.row_tb[pi] = split == 1 ? tb : 0;
+  if (split == 1) {
     const size_t budget = 72 * 1024, full = (size_t)g.ny * g.nxh * 2 * rb;
     const int c = (int)((full + budget - 1) / budget);
     g.col_w[pi] = (g.nxh + c - 1) / c;
@@ -695,8 +697,9 @@ int autotune_lane(itp_handle h, int k, double tau, std::string& rep) {
   auto prop = [&]() { return propagate_lane<R>(h, k, tau); };
   // 1. plane-pass form: whole planes (where they fit) or row + column passes
   {
-    std::vector<std::pair<int, int>> forms;   // (split, tb)
+    std::vector<std::pair<int, int>> forms;   // (plane form, row block)
     if (plane_smem_bytes(g, rb) <= kSmemLimit) forms.push_back({0, 0});
+    if (pi == 0 && g.nx == 256 && g.ny == 256) forms.push_back({2, 0});
     for (int tb : {32, 16, 8})
       if ((g.ny / 2) % tb == 0 && ((size_t)tb * g.pp + g.nx) * 2 * rb <= 96 * 1024 &&
           (tb != 32 || (pi == 0 && g.nx == 256)))
@@ -710,8 +713,9 @@ int autotune_lane(itp_handle h, int k, double tau, std::string& rep) {
       if (set_tuning(h, cur) != ITP_OK) continue;
       float ms = 0.f;
       ITP_TRY(time_ms(h, 2, &ms, prop));
-      snprintf(buf, sizeof(buf), " %s=%.3fms", split ? ("split" + std::to_string(tb)).c_str()
-                                                     : "whole", ms);
+      snprintf(buf, sizeof(buf), " %s=%.3fms",
+               split == 1 ? ("split" + std::to_string(tb)).c_str()
+                          : (split == 2 ? "cluster2" : "whole"), ms);
       rep += buf;
       if (ms < best_ms) {
         best_ms = ms;

@@ -127,3 +127,44 @@ def test_batch_recaptures_after_a_shape_change():
         assert b.kernel_launches - n0 > n0
         assert np.max(np.abs(E1[0] - E1[1])) < 1e-12 * np.max(np.abs(E1[0]))
         assert np.all(np.isfinite(E0[0]))
+
+
+@pytest.mark.parametrize("dims", [(256, 256, 4), (256, 256, 1)])
+def test_cluster_planes_match_oracle(dims):
+    """256 x 256 FP32 planes on two-CTA clusters (plane form 2): propagation,
+    orthonormalisation and Ritz values against the oracle, 3D and planar."""
+    from itp_workloads import planar
+    nx, ny, nz = dims
+    g = Grid(nx, ny, nz, 20.0, 18.0, 6.0) if nz > 1 else planar(nx, ny, 20.0, 18.0)
+    V = wells_problem(g)
+    m = 3
+    psi = seeded_states(g, m)
+    order, tau = 6, 0.3
+    with P.ItpGrid(nx, ny, nz, g.lx, g.ly, g.lz, m, 0, P.ITP_MIXED) as h:
+        h.set_potential(V)
+        t = h.get_tuning()
+        h.set_tuning(t["pencil_w"], 2, 0, t["gram_ctas"])
+        assert h.get_tuning()["split"] == 2
+        h.set_states(psi)
+        h.propagate(order, tau)
+        phi = h.get_phi()
+        h.orthonormalize()
+        E = h.energies("values")
+    ref = O.propagate(psi, V, g, order, tau)
+    assert _relerr(phi, ref) < propagate_tolerance(order, g.n_points, "mixed")
+    psi_ref, _ = O.cholesky_orthonormalize(ref, g.dV)
+    E_ref, _, _ = O.energies(psi_ref, V, g, ritz=True)
+    assert np.max(np.abs(E - E_ref)) < 1e-5 * np.max(np.abs(E_ref))
+
+
+def test_cluster_planes_only_where_they_apply():
+    with P.ItpGrid(256, 256, 4, 20.0, 20.0, 4.0, 2, 0, P.ITP_FP64) as h:
+        t = h.get_tuning()
+        with pytest.raises(P.ItpError):
+            h.set_tuning(t["pencil_w"], 2, 0, t["gram_ctas"])   # FP64 lane
+    with P.ItpGrid(128, 128, 4, 20.0, 20.0, 4.0, 2, 0, P.ITP_MIXED) as h:
+        t = h.get_tuning()
+        with pytest.raises(P.ItpError):
+            h.set_tuning(t["pencil_w"], 2, 0, t["gram_ctas"])   # not 256 x 256
+        with pytest.raises(P.ItpError):
+            h.set_tuning(t["pencil_w"], 3, 0, t["gram_ctas"])
