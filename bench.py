@@ -663,6 +663,57 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    # ---- end to end through the C ABI with host buffers (first, in a clean process) --
+    e2e = None
+    if not args.no_e2e:
+        K = min(args.steps, 5)
+        h = P.ItpGrid(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, w["n_states"], w["n_guard"],
+                      P.ITP_MIXED)   # the library's own stream, as a host-side caller has
+        h.set_potential(V)
+        h.set_states(psi)
+        h.autotune(order, tau)
+        pin_in = torch.from_numpy(psi).pin_memory()
+        pin_out = torch.empty_like(pin_in).pin_memory()
+        E_host = np.empty(m)
+        lib = P.load()
+        h.set_states(psi)
+        for _ in range(3):   # warm-up of the whole end-to-end sequence, copies included
+            lib.itp_set_states(h.h, pin_in.data_ptr())
+            P.itp_step(h.h, order, tau, P.ITP_RITZ_VALUES, E_host)
+            lib.itp_get_states(h.h, pin_out.data_ptr())
+        barrier()
+        phases = {"set_states": 0.0, "step": 0.0, "get_states": 0.0}
+        t0 = time.perf_counter()
+        for _ in range(K):
+            ta = time.perf_counter()
+            lib.itp_set_states(h.h, pin_in.data_ptr())     # host -> device, [m][N] FP64
+            tb = time.perf_counter()
+            P.itp_step(h.h, order, tau, P.ITP_RITZ_VALUES, E_host)   # energies -> host
+            tc = time.perf_counter()
+            lib.itp_get_states(h.h, pin_out.data_ptr())    # device -> host, synchronises
+            td = time.perf_counter()
+            phases["set_states"] += tb - ta
+            phases["step"] += tc - tb
+            phases["get_states"] += td - tc
+        barrier()
+        t_e2e = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": replicas_value(m * K, t_e2e, world), "unit": "state-steps/s",
+               "h2d_bytes_per_step": int(psi.nbytes),
+               "d2h_bytes_per_step": int(psi.nbytes + E_host.nbytes), "steps": K,
+               "calls": "itp_set_states (pinned host) + itp_step + itp_get_states (pinned host)",
+               "host_ms_per_step": {k: round(1e3 * v / K, 2) for k, v in phases.items()}}
+        # the raw copy rate of the same pinned buffers, for comparison
+        dev = torch.empty(pin_in.shape, dtype=pin_in.dtype, device="cuda")
+        dev.copy_(pin_in, non_blocking=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dev.copy_(pin_in, non_blocking=True)
+        pin_out.copy_(dev, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e["raw_copy_gbs_h2d_plus_d2h"] = round(2 * psi.nbytes / (time.perf_counter() - t0) / 1e9, 1)
+        del dev, pin_in, pin_out
+        h.close()
+
     # ---- headline: mixed path, states resident in HBM --------------------------
     h = P.ItpGrid(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, w["n_states"], w["n_guard"],
                   P.ITP_MIXED, cuda_stream=stream.cuda_stream)
@@ -770,56 +821,6 @@ def main():
         b.synchronize()
         prop_ms[name] = round(a.elapsed_time(b) / 3, 3)
     h.close()
-
-    # ---- end to end through the C ABI with host buffers -----------------------
-    e2e = None
-    if not args.no_e2e:
-        K = min(args.steps, 5)
-        h = P.ItpGrid(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, w["n_states"], w["n_guard"],
-                      P.ITP_MIXED)   # the library's own stream, as a host-side caller has
-        h.set_potential(V)
-        h.set_tuning(**tuned)
-        pin_in = torch.from_numpy(psi).pin_memory()
-        pin_out = torch.empty_like(pin_in).pin_memory()
-        E_host = np.empty(m)
-        lib = P.load()
-        h.set_states(psi)
-        for _ in range(3):   # warm-up of the whole end-to-end sequence, copies included
-            lib.itp_set_states(h.h, pin_in.data_ptr())
-            P.itp_step(h.h, order, tau, P.ITP_RITZ_VALUES, E_host)
-            lib.itp_get_states(h.h, pin_out.data_ptr())
-        barrier()
-        phases = {"set_states": 0.0, "step": 0.0, "get_states": 0.0}
-        t0 = time.perf_counter()
-        for _ in range(K):
-            ta = time.perf_counter()
-            lib.itp_set_states(h.h, pin_in.data_ptr())     # host -> device, [m][N] FP64
-            tb = time.perf_counter()
-            P.itp_step(h.h, order, tau, P.ITP_RITZ_VALUES, E_host)   # energies -> host
-            tc = time.perf_counter()
-            lib.itp_get_states(h.h, pin_out.data_ptr())    # device -> host, synchronises
-            td = time.perf_counter()
-            phases["set_states"] += tb - ta
-            phases["step"] += tc - tb
-            phases["get_states"] += td - tc
-        barrier()
-        t_e2e = max_over_ranks(time.perf_counter() - t0)
-        e2e = {"value": replicas_value(m * K, t_e2e, world), "unit": "state-steps/s",
-               "h2d_bytes_per_step": int(psi.nbytes),
-               "d2h_bytes_per_step": int(psi.nbytes + E_host.nbytes), "steps": K,
-               "calls": "itp_set_states (pinned host) + itp_step + itp_get_states (pinned host)",
-               "host_ms_per_step": {k: round(1e3 * v / K, 2) for k, v in phases.items()}}
-        # the raw copy rate of the same pinned buffers, for comparison
-        dev = torch.empty(pin_in.shape, dtype=pin_in.dtype, device="cuda")
-        dev.copy_(pin_in, non_blocking=True)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        dev.copy_(pin_in, non_blocking=True)
-        pin_out.copy_(dev, non_blocking=True)
-        torch.cuda.synchronize()
-        e2e["raw_copy_gbs_h2d_plus_d2h"] = round(2 * psi.nbytes / (time.perf_counter() - t0) / 1e9, 1)
-        del dev
-        h.close()
 
     # ---- the FP64 form of the same workload -----------------------------------
     fp64 = None
