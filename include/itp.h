@@ -238,9 +238,10 @@ int itp_profile_read(itp_handle h, int kind, long long* launches, double* total_
  *   [ITP_TUNE_SPLIT]     plane-pass form: 0: one CTA per plane for the x
  *                        and y transforms (only where the plane fits one
  *                        CTA); 1: row passes (x) and column passes (y), three
- *                        HBM round trips; 2: a cluster of two CTAs per plane
- *                        exchanging rows through distributed shared memory,
- *                        one round trip (256 x 256 planes, FP32 lane only)
+ *                        HBM round trips; 2 or 3: a cluster of two or four
+ *                        CTAs per plane exchanging rows through distributed
+ *                        shared memory, one round trip (256 x 256 planes,
+ *                        FP32 lane only)
  *   [ITP_TUNE_ROW_TB]    row pairs per row-pass CTA with ITP_TUNE_SPLIT = 1
  *                        (0 otherwise):
  *                        8, 16, or 32 (32: FP32 with nx = 256 only); it

@@ -994,6 +994,148 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kC2Threads, 1)
   yB_fwd_global(G, sm, static_cast<C*>(a.spec) + spec_off + rank * G.nxh, a.kin);
 }
 
+// The same planes on a cluster of four CTAs, each holding 64 real-space rows
+// (y = 64 r + n) or the spectrum rows ky = 4 j + r, 75 KB of shared memory,
+// so that three CTAs share an SM: a radix-4 step across the cluster plus
+// local 64-point transforms,
+//   forward:  X(4j+r) = FFT64[ w^(nr) sum_q x_q(n) (-i)^(qr) ](j),  x_q(n) = x(64q + n);
+//   inverse:  x(64q+n) = sum_r i^(qr) w^(-nr) O_r(n),  O_r = IFFT64 of the rows 4j+r.
+// The exchange reads all four CTAs' values of a chunk of elements, then a
+// cluster barrier, then each CTA writes its own result for the chunk.
+constexpr int kC4Threads = 256;
+
+template <int DIR, typename G_>
+__device__ __forceinline__ void c4_exchange(const G_& G, float2* sm, const float2* tw256,
+                                            cg::cluster_group& cl, int rank) {
+  constexpr int NT = G_::NT;
+  constexpr int PER = 8;   // elements per thread and chunk
+  const float2* rs[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) rs[q] = cl.map_shared_rank(sm, q);
+  const int total = 64 * G.nxh;
+  cl.sync();   // every CTA's local stage is complete
+  for (int c0 = 0; c0 < total; c0 += NT * PER) {
+    float2 v[PER][4];
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      const int e = c0 + (int)threadIdx.x + NT * p;
+      if (e < total) {
+        const int n = e / G.nxh, t = e - n * G.nxh;
+        const int pos = G.col(t, n);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[p][q] = rs[q][pos];
+      }
+    }
+    cl.sync();   // the chunk is read everywhere before any CTA overwrites it
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      const int e = c0 + (int)threadIdx.x + NT * p;
+      if (e < total) {
+        const int n = e / G.nxh, t = e - n * G.nxh;
+        float2 a0 = v[p][0], a1 = v[p][1], a2 = v[p][2], a3 = v[p][3];
+        if (DIR > 0) {   // inverse: twiddle w^(-rn) first
+          a1 = cmulc(a1, tw256[n]);
+          a2 = cmulc(a2, tw256[2 * n]);
+          a3 = cmulc(a3, tw256[3 * n]);
+        }
+        const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2);
+        const float2 s13 = cadd(a1, a3), d13 = csub(a1, a3);
+        float2 r;
+        // i*d = (-d.y, d.x), -i*d = (d.y, -d.x)
+        const int k = DIR < 0 ? rank : (4 - rank) & 3;   // inverse uses i^(qr) = (-i)^(-qr)
+        if (k == 0) r = cadd(s02, s13);
+        else if (k == 2) r = csub(s02, s13);
+        else if (k == 1) r = float2{d02.x + d13.y, d02.y - d13.x};
+        else r = float2{d02.x - d13.y, d02.y + d13.x};
+        if (DIR < 0 && rank > 0) r = cmul(r, tw256[rank * n]);
+        sm[G.col(t, n)] = r;
+      }
+    }
+  }
+}
+
+template <int MODE>
+__global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kC4Threads, 3)
+    plane_c4_kernel(const GridDesc g, const PlaneArgs<float> a) {
+  using R = float;
+  using C = float2;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  PlaneGeo<R, 256, 64, kC4Threads> G(g);
+  G.gpair = 128;
+  G.srs = 4 * G.nxh;      // this CTA's spectrum rows ky = 4 j + rank
+  G.kym = 4;
+  G.kya = rank;
+  C* sm = reinterpret_cast<C*>(smraw);
+  C* twx = sm + G.npair * G.pp;   // 256 roots (x)
+  C* twy = twx + 256;             // 64 roots of the local transforms: w^(4j)
+  C* tw256 = twy + 64;            // 256 roots w^m of the radix-4 step
+  const C* tg = static_cast<const C*>(a.twy);
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+    twx[i] = static_cast<const C*>(a.twx)[i];
+    tw256[i] = tg[i];
+  }
+  for (int i = threadIdx.x; i < 64; i += blockDim.x) twy[i] = tg[4 * i];
+  const int z = blockIdx.x >> 2, s = blockIdx.y;
+  const long long plane_pts = 256LL * 256;
+  const long long real_off = (long long)s * g.n_points + (long long)z * plane_pts;
+  const long long spec_off = ((long long)s * g.nz + z) * 256LL * G.nxh;
+  const long long fac_off = (long long)z * plane_pts;
+  const int t0 = 32 * rank;   // first (global) row pair of this CTA
+  __syncthreads();
+
+  if constexpr (MODE == PLANE_FWD_REAL) {
+    const C* src = reinterpret_cast<const C*>(a.in_real + real_off) + t0;
+    const C* f = a.f_in ? reinterpret_cast<const C*>(a.f_in + fac_off) + t0 : nullptr;
+    xA_fwd_global(G, sm, src, f, twx);
+    __syncthreads();
+  } else {
+    yB_inv_global(G, sm, static_cast<const C*>(a.spec) + spec_off + rank * G.nxh, twy);
+    __syncthreads();
+    yA<1>(G, sm, twy);
+    __syncthreads();
+    c4_exchange<1>(G, sm, tw256, cl, rank);
+    __syncthreads();
+    xB_inv_merge(G, sm, twx);
+    __syncthreads();
+    if constexpr (MODE == PLANE_MERGED) {
+      EpiMerged<R> epi{reinterpret_cast<const C*>(a.f_mid + fac_off) + t0, G.gpair, G.ax.r1};
+      xA_inv_then(G, sm, twx, epi);
+      __syncthreads();
+    } else if constexpr (MODE == PLANE_TERM) {
+      EpiTerm<R> epi{reinterpret_cast<const C*>(a.f_out + fac_off) + t0,
+                     static_cast<C*>(a.spec) + spec_off + t0, (R)a.coef, G.gpair, G.ax.r1};
+      xA_inv_then(G, sm, twx, epi);
+      return;
+    } else if constexpr (MODE == PLANE_COMBINE) {
+      EpiCombinePair<R> epi{reinterpret_cast<const C*>(a.f_out + fac_off) + t0,
+                            reinterpret_cast<float4*>(a.acc + real_off) + t0,
+                            a.phi_out ? reinterpret_cast<C*>(a.phi_out + real_off) + t0 : nullptr,
+                            (float)a.coef, a.acc_init, G.gpair, G.ax.r1};
+      xA_inv_then(G, sm, twx, epi);
+      return;
+    } else if constexpr (MODE == PLANE_HPSI) {
+      EpiHpsi<R> epi{reinterpret_cast<const C*>(a.in_real + real_off) + t0,
+                     reinterpret_cast<const double2*>(a.V + fac_off) + t0,
+                     reinterpret_cast<double2*>(a.acc + real_off) + t0,
+                     reinterpret_cast<const C*>(a.V_r + fac_off) + t0,
+                     reinterpret_cast<C*>(a.phi_out + real_off) + t0, G.gpair, G.ax.r1};
+      xA_inv_then(G, sm, twx, epi);
+      return;
+    } else {
+      return;
+    }
+  }
+  xB_fwd_split(G, sm, twx);
+  __syncthreads();
+  c4_exchange<-1>(G, sm, tw256, cl, rank);
+  __syncthreads();
+  yA<-1>(G, sm, twy);
+  __syncthreads();
+  yB_fwd_global(G, sm, static_cast<C*>(a.spec) + spec_off + rank * G.nxh, a.kin);
+}
+
 // ----------------------------------------------------------------------------
 // Split plane passes, for planes whose half spectrum does not fit one CTA's
 // shared memory (nx = ny = 256 in FP32, >= 192 in FP64).  A row pass does
@@ -1397,6 +1539,34 @@ cudaError_t launch_plane(const GridDesc& g, const PlaneArgs<R>& a, cudaStream_t 
   // FP32 H psi passes write FP32 (potential and output in R)
   if (a.mode == PLANE_HPSI && sizeof(R) == 4 && (!a.V_r || !a.phi_out))
     return cudaErrorInvalidValue;
+  if (g.split_planes[sizeof(R) == 4 ? 0 : 1] == 3) {
+    // 256 x 256 FP32 planes on four-CTA clusters
+    if constexpr (sizeof(R) == 4) {
+      if (g.nx != 256 || g.ny != 256) return cudaErrorInvalidValue;
+      const size_t smem = ((size_t)32 * row_pitch(256) + 576) * sizeof(float2);
+      dim3 grid(4 * g.nz, a.m);
+      cudaError_t e;
+      switch (a.mode) {
+#define ITP_C4_CASE(M)                                                      \
+  case M:                                                                   \
+    e = set_smem(plane_c4_kernel<M>, smem);                                 \
+    if (e != cudaSuccess) return e;                                         \
+    plane_c4_kernel<M><<<grid, kC4Threads, smem, st>>>(g, a);               \
+    break;
+        ITP_C4_CASE(PLANE_FWD_REAL)
+        ITP_C4_CASE(PLANE_MERGED)
+        ITP_C4_CASE(PLANE_COMBINE)
+        ITP_C4_CASE(PLANE_HPSI)
+        ITP_C4_CASE(PLANE_TERM)
+#undef ITP_C4_CASE
+        default:
+          return cudaErrorInvalidValue;
+      }
+      return cudaGetLastError();
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  }
   if (g.split_planes[sizeof(R) == 4 ? 0 : 1] == 2) {
     // 256 x 256 FP32 planes on two-CTA clusters
     if constexpr (sizeof(R) == 4) {

@@ -632,11 +632,11 @@ int set_tuning(itp_handle h, const int* t) {
             chunks = t[ITP_TUNE_GRAM];
   if (w < 1 || w > g.nxh || ((size_t)g.nz * w + g.nz) * 16 > kSmemLimit)
     return fail(h, ITP_ERR_ARG, "pencil width %d not in 1..%d or too large", w, g.nxh);
-  if (split < 0 || split > 2) return fail(h, ITP_ERR_ARG, "plane form must be 0, 1 or 2");
+  if (split < 0 || split > 3) return fail(h, ITP_ERR_ARG, "plane form must be 0, 1, 2 or 3");
   if (!split && plane_smem_bytes(g, rb) > kSmemLimit)
     return fail(h, ITP_ERR_ARG, "a %dx%d plane does not fit one CTA", g.nx, g.ny);
-  if (split == 2 && !(pi == 0 && g.nx == 256 && g.ny == 256))
-    return fail(h, ITP_ERR_ARG, "two-CTA cluster planes are 256x256 FP32 only");
+  if (split >= 2 && !(pi == 0 && g.nx == 256 && g.ny == 256))
+    return fail(h, ITP_ERR_ARG, "cluster planes are 256x256 FP32 only");
   if (split == 1 && !(tb == 8 || tb == 16 || tb == 32) )
     return fail(h, ITP_ERR_ARG, "row-pass block %d not 8, 16 or 32", tb);
   if (split == 1 && ((g.ny / 2) % tb != 0 || ((size_t)tb * g.pp + g.nx) * 2 * rb > 96 * 1024 ||
@@ -699,7 +699,10 @@ int autotune_lane(itp_handle h, int k, double tau, std::string& rep) {
   {
     std::vector<std::pair<int, int>> forms;   // (plane form, row block)
     if (plane_smem_bytes(g, rb) <= kSmemLimit) forms.push_back({0, 0});
-    if (pi == 0 && g.nx == 256 && g.ny == 256) forms.push_back({2, 0});
+    if (pi == 0 && g.nx == 256 && g.ny == 256) {
+      forms.push_back({2, 0});
+      forms.push_back({3, 0});
+    }
     for (int tb : {32, 16, 8})
       if ((g.ny / 2) % tb == 0 && ((size_t)tb * g.pp + g.nx) * 2 * rb <= 96 * 1024 &&
           (tb != 32 || (pi == 0 && g.nx == 256)))
@@ -715,7 +718,7 @@ int autotune_lane(itp_handle h, int k, double tau, std::string& rep) {
       ITP_TRY(time_ms(h, 2, &ms, prop));
       snprintf(buf, sizeof(buf), " %s=%.3fms",
                split == 1 ? ("split" + std::to_string(tb)).c_str()
-                          : (split == 2 ? "cluster2" : "whole"), ms);
+                          : (split == 2 ? "cluster2" : (split == 3 ? "cluster4" : "whole")), ms);
       rep += buf;
       if (ms < best_ms) {
         best_ms = ms;

@@ -129,10 +129,12 @@ def test_batch_recaptures_after_a_shape_change():
         assert np.all(np.isfinite(E0[0]))
 
 
+@pytest.mark.parametrize("form", [2, 3])
 @pytest.mark.parametrize("dims", [(256, 256, 4), (256, 256, 1)])
-def test_cluster_planes_match_oracle(dims):
-    """256 x 256 FP32 planes on two-CTA clusters (plane form 2): propagation,
-    orthonormalisation and Ritz values against the oracle, 3D and planar."""
+def test_cluster_planes_match_oracle(dims, form):
+    """256 x 256 FP32 planes on two- and four-CTA clusters (plane forms 2,
+    3): propagation, orthonormalisation and Ritz values against the oracle,
+    3D and planar."""
     from itp_workloads import planar
     nx, ny, nz = dims
     g = Grid(nx, ny, nz, 20.0, 18.0, 6.0) if nz > 1 else planar(nx, ny, 20.0, 18.0)
@@ -143,8 +145,8 @@ def test_cluster_planes_match_oracle(dims):
     with P.ItpGrid(nx, ny, nz, g.lx, g.ly, g.lz, m, 0, P.ITP_MIXED) as h:
         h.set_potential(V)
         t = h.get_tuning()
-        h.set_tuning(t["pencil_w"], 2, 0, t["gram_ctas"])
-        assert h.get_tuning()["split"] == 2
+        h.set_tuning(t["pencil_w"], form, 0, t["gram_ctas"])
+        assert h.get_tuning()["split"] == form
         h.set_states(psi)
         h.propagate(order, tau)
         phi = h.get_phi()
@@ -167,4 +169,6 @@ def test_cluster_planes_only_where_they_apply():
         with pytest.raises(P.ItpError):
             h.set_tuning(t["pencil_w"], 2, 0, t["gram_ctas"])   # not 256 x 256
         with pytest.raises(P.ItpError):
-            h.set_tuning(t["pencil_w"], 3, 0, t["gram_ctas"])
+            h.set_tuning(t["pencil_w"], 3, 0, t["gram_ctas"])   # not 256 x 256
+        with pytest.raises(P.ItpError):
+            h.set_tuning(t["pencil_w"], 4, 0, t["gram_ctas"])
