@@ -255,7 +255,7 @@ def ho_closed_shells(n):
 
 
 def time_to_tol(P, precision, tol=1e-8, order=12, tau=0.5, n=120, guard=8,
-                max_fp32=400, max_fp64=200, plateau_rel=1e-5):
+                max_fp32=400, max_fp64=200, plateau_rel=1e-5, polish_order=None):
     """Wall time from itp_set_states of seeded random states until every one
     of the n lowest Ritz energies is within tol of its exact value (3D
     harmonic oscillator, 128^3 grid, box [-8,8)^3, n = 120 = eight closed
@@ -289,7 +289,7 @@ def time_to_tol(P, precision, tol=1e-8, order=12, tau=0.5, n=120, guard=8,
         dEs = []
         extra = None
         while steps32 < max_fp32:
-            E = h.step(order, tau, ritz="values")
+            E = h.step_graph(order, tau)
             steps32 += 1
             err = float(np.max(np.abs(E[:n] - E_ref)))
             if err < tol:
@@ -311,12 +311,12 @@ def time_to_tol(P, precision, tol=1e-8, order=12, tau=0.5, n=120, guard=8,
                 dEs.append(dE)
             E_prev = E
         while err >= tol and steps64 < max_fp64:
-            _, E = h.polish(order, tau, 1e-300, 1)
+            _, E = h.polish(polish_order or order, tau, 1e-300, 1)
             steps64 += 1
             err = float(np.max(np.abs(E[:n] - E_ref)))
     else:
         while err >= tol and steps64 < max_fp64:
-            E = h.step(order, tau, ritz="values")
+            E = h.step_graph(order, tau)
             steps64 += 1
             err = float(np.max(np.abs(E[:n] - E_ref)))
     h.synchronize()
@@ -856,6 +856,12 @@ def main():
                "mixed": time_to_tol(P, P.ITP_MIXED),
                "fp64": time_to_tol(P, P.ITP_FP64)}
         ttt["speedup_mixed_vs_fp64"] = ttt["fp64"]["seconds"] / ttt["mixed"]["seconds"]
+        # order 6 (the fastest order per converged state on one GB300, as the
+        # paper found on one processor): FP32 steps at order 6, FP64 polish at
+        # order 12; and the FP64 path at order 6
+        ttt["order6"] = {"mixed_fp32_order6_polish_order12":
+                         time_to_tol(P, P.ITP_MIXED, order=6, polish_order=12),
+                         "fp64_order6": time_to_tol(P, P.ITP_FP64, order=6)}
         # the same problem with the adaptive iteration of Sec. III
         ttt["adaptive"] = {"mixed": adaptive_to_tol(P, P.ITP_MIXED)}
         if args.adaptive_fp64:   # about two minutes on one GB300
