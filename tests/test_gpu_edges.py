@@ -1,0 +1,40 @@
+"""Edge cases of the state count: a single state (1 x 1 overlap, Cholesky and
+eigenproblem) and the largest block (128 states) in FP64, against the oracle."""
+import numpy as np
+import pytest
+
+from itp_workloads import Grid
+from oracle import itp_oracle as O
+
+from gpu_helpers import propagate_tolerance, seeded_states, wells_problem
+
+pytestmark = pytest.mark.gpu
+
+import paper_0809_3739_gb300 as P  # noqa: E402
+
+PREC = {"fp64": P.ITP_FP64, "mixed": P.ITP_MIXED}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("m", [1, 128])
+def test_state_count_extremes(prec, m):
+    g = Grid(16, 12, 8, 8.0, 7.0, 6.0)
+    V = wells_problem(g)
+    psi = seeded_states(g, m)
+    order, tau = 8, 0.05   # a short step keeps 128 states of 1536 points well conditioned
+    with P.ItpGrid(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, m, 0, PREC[prec]) as h:
+        h.set_potential(V)
+        h.set_states(psi)
+        h.propagate(order, tau)
+        phi = h.get_phi()
+        h.orthonormalize()
+        E = h.energies("values")
+        got = h.get_states()
+    ref = O.propagate(psi, V, g, order, tau)
+    err = np.max(np.abs(phi - ref)) / np.max(np.abs(ref))
+    assert err < propagate_tolerance(order, g.n_points, prec)
+    psi_ref, _ = O.cholesky_orthonormalize(ref, g.dV)
+    E_ref, _, _ = O.energies(psi_ref, V, g, ritz=True)
+    assert np.max(np.abs(E - E_ref)) < (1e-11 if prec == "fp64" else 1e-5) * np.max(np.abs(E_ref))
+    S = got @ got.T * g.dV
+    assert np.max(np.abs(S - np.eye(m))) < (1e-12 if prec == "fp64" else 2e-5)
