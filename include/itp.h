@@ -142,6 +142,30 @@ int itp_energies(itp_handle h, double* E_host, int flags);
  * Per-kernel profiling (itp_profile) does not see graph replays. */
 int itp_step(itp_handle h, int order, double tau, int flags, double* E_host);
 
+/* One whole step between host buffers: the result of
+ *     itp_set_states(psi_in_host); itp_step(order, tau, flags, E_host);
+ *     itp_get_states(psi_out_host)
+ * (the same kernels on the same values, so bit for bit the same states and
+ * energies), with the copies overlapped with the device work.  The states
+ * move in 4 chunks of whole states (fewer if m < 4) on a second stream of the
+ * library's own: chunk c is copied in while chunk c-1 is propagated (Eq. 3
+ * acts on each state alone); after the orthonormalisation (Eq. 4, which
+ * needs every state) the result goes out chunk by chunk while the energies
+ * are computed.
+ *   psi_in_host   [m][nz][ny][nx] doubles, read (not necessarily orthonormal)
+ *   psi_out_host  [m][nz][ny][nx] doubles, written: the orthonormalised
+ *                 states after the step; may be psi_in_host itself
+ *   E_host        (nullable) the m energies, as itp_step
+ * flags: 0 or ITP_RITZ_VALUES.  Page-locked host buffers (cudaHostAlloc or
+ * cudaHostRegister) are needed for the copies to overlap; pageable ones
+ * give the same results with the copies serialised.  The first call
+ * allocates an FP64 staging block of m x N doubles and the copy stream.
+ * Work already queued on the handle's stream runs first.  Synchronises;
+ * neither buffer is touched after the call returns, also on failure.  Runs
+ * kernel by kernel (not from a graph); itp_profile sees every launch. */
+int itp_step_host(itp_handle h, int order, double tau, int flags, const double* psi_in_host,
+                  double* psi_out_host, double* E_host);
+
 /* Mixed precision only: switch the states to FP64 and iterate FP64 steps
  * (propagate, orthonormalise, Ritz values) until
  * max_{j<n_states} |E_j - E_j(previous)| < tol or max_steps steps, then

@@ -9,5 +9,5 @@ from .itp import (ITP_FP64, ITP_MIXED, ITP_RITZ, ITP_RITZ_VALUES, ITP_STEP_FP64,
                   itp_last_error, itp_orthonormalize, itp_orthonormalize_noalloc, itp_polish,
                   itp_profile, itp_profile_read, itp_propagate, itp_propagate_romberg6,
                   itp_set_potential,
-                  itp_set_states, itp_set_states_device, itp_solve_adaptive, itp_step,
+                  itp_set_states, itp_set_states_device, itp_solve_adaptive, itp_step, itp_step_host,
                   itp_synchronize, load)

@@ -21,6 +21,7 @@ namespace {
 
 constexpr int kMaxStates = 128;
 constexpr int kMaxTerms = 6;   // order <= 12
+constexpr int kHostChunks = 4; // state chunks of the host-buffer step (copy/compute overlap)
 constexpr size_t kSmemLimit = 227 * 1024;
 
 template <typename R>
@@ -87,6 +88,11 @@ struct itp_grid {
   struct ProfEvent { int kind; cudaEvent_t start, stop; };
   std::vector<ProfEvent> prof_events;
   size_t prof_used = 0;
+  // host-buffer step (itp_step_host): copy stream, FP64 staging block in the
+  // user layout, events (per chunk: input copied, output staged; start; end)
+  cudaStream_t cst = nullptr;
+  double* hstage = nullptr;   // [m][N]
+  cudaEvent_t hev[2 * kHostChunks + 2] = {};
 };
 
 namespace {
@@ -307,7 +313,7 @@ int prepare_tables(itp_handle h, Lane<R>& L, int k, double tau) {
 // contribution c_i f u_i over it, and sums the contributions once in FP64.
 template <typename R>
 int propagate_lane(itp_handle h, int k, double tau, int s0 = 0, const R* in = nullptr,
-                   R* out = nullptr) {
+                   R* out = nullptr, int s1 = -1) {
   Lane<R>& L = lane_of<R>(h);
   ITP_TRY(prepare_tables<R>(h, L, k, tau));
   const GridDesc& g = h->g;
@@ -323,8 +329,8 @@ int propagate_lane(itp_handle h, int k, double tau, int s0 = 0, const R* in = nu
       }
     }
   }
-  // states s0..m-1 only (the leading s0 states are kept fixed)
-  const int ms = h->m - s0;
+  // states s0..s1-1 only (s1 < 0: to the last state; the others are kept)
+  const int ms = (s1 < 0 ? h->m : s1) - s0;
   const long long so = s0;
   auto at_state = [&](void* w) {
     return static_cast<void*>(static_cast<char*>(w) + so * g.n_half * 2 * sizeof(R));
@@ -521,11 +527,8 @@ int energies_lane(itp_handle h, int flags) {
   return ITP_OK;
 }
 
-// Read and clear the device status word (synchronises the stream).
-int collect_status(itp_handle h) {
-  ITP_CUDA(h, cudaMemcpyAsync(h->status_host, h->status, sizeof(int), cudaMemcpyDeviceToHost,
-                              h->st));
-  ITP_CUDA(h, cudaStreamSynchronize(h->st));
+// Report and clear a device status word already copied to status_host.
+int take_status(itp_handle h) {
   const int s = *h->status_host;
   if (s) {
     ITP_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->st));
@@ -534,6 +537,14 @@ int collect_status(itp_handle h) {
     if (s & 4) return fail(h, ITP_ERR_TIMEOUT, "a bounded tensor-core pipeline wait expired");
   }
   return ITP_OK;
+}
+
+// Read and clear the device status word (synchronises the stream).
+int collect_status(itp_handle h) {
+  ITP_CUDA(h, cudaMemcpyAsync(h->status_host, h->status, sizeof(int), cudaMemcpyDeviceToHost,
+                              h->st));
+  ITP_CUDA(h, cudaStreamSynchronize(h->st));
+  return take_status(h);
 }
 
 // Make the lane of precision R hold the states (converting if needed).
@@ -896,6 +907,82 @@ int propagate_romberg6_lane(itp_handle h, double tau) {
   return ITP_OK;
 }
 
+// ---- one step between host buffers (itp_step_host) --------------------------------
+int host_step_resources(itp_handle h) {
+  if (h->cst) return ITP_OK;
+  if (!h->hstage)
+    ITP_CUDA(h, cudaMalloc(&h->hstage, (size_t)h->m * h->g.n_points * sizeof(double)));
+  for (auto& e : h->hev)
+    if (!e) ITP_CUDA(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  // non-blocking: no implicit ordering against a legacy default stream; the
+  // events below order the two streams
+  ITP_CUDA(h, cudaStreamCreateWithFlags(&h->cst, cudaStreamNonBlocking));
+  return ITP_OK;
+}
+
+// The states travel in kHostChunks chunks of whole states.  The copy stream
+// brings chunk c in while the handle's stream propagates chunk c-1 (the
+// propagation of a state needs no other state); the orthonormalisation
+// then needs all of them; the staged result goes out chunk by chunk on the
+// copy stream while the energies are computed.  Every kernel is the one
+// itp_set_states + itp_step + itp_get_states would run on the same states.
+template <typename R>
+int step_host_work(itp_handle h, int k, double tau, int flags, const double* in,
+                   double* out) {
+  Lane<R>& L = lane_of<R>(h);
+  const GridDesc& g = h->g;
+  const size_t N = g.n_points;
+  const int C = std::min(kHostChunks, h->m);
+  auto first = [&](int c) { return (int)((long long)c * h->m / C); };
+  cudaEvent_t* ev_in = h->hev;
+  cudaEvent_t* ev_out = h->hev + kHostChunks;
+  cudaEvent_t ev_go = h->hev[2 * kHostChunks], ev_done = h->hev[2 * kHostChunks + 1];
+  // the copies start after the work already queued on the handle's stream
+  ITP_CUDA(h, cudaEventRecord(ev_go, h->st));
+  ITP_CUDA(h, cudaStreamWaitEvent(h->cst, ev_go, 0));
+  for (int c = 0; c < C; ++c) {
+    const size_t off = (size_t)first(c) * N, cnt = (size_t)(first(c + 1) - first(c)) * N;
+    ITP_CUDA(h, cudaMemcpyAsync(h->hstage + off, in + off, cnt * sizeof(double),
+                                cudaMemcpyHostToDevice, h->cst));
+    ITP_CUDA(h, cudaEventRecord(ev_in[c], h->cst));
+  }
+  for (int c = 0; c < C; ++c) {
+    const int s0 = first(c), s1 = first(c + 1);
+    ITP_CUDA(h, cudaStreamWaitEvent(h->st, ev_in[c], 0));
+    // user layout [z][y][x] -> internal [z][x][y], rounded to R
+    ITP_LAUNCH(h, ITP_KERNEL_OTHER,
+               (launch_transpose_planes<double, R>(h->hstage + (size_t)s0 * N,
+                                                   L.psi + (size_t)s0 * N,
+                                                   (long long)(s1 - s0) * g.nz, g.ny, g.nx,
+                                                   h->st)));
+    ITP_TRY(propagate_lane<R>(h, k, tau, s0, nullptr, nullptr, s1));
+  }
+  ITP_TRY(orthonormalize_lane<R>(h));
+  for (int c = 0; c < C; ++c) {
+    const int s0 = first(c), s1 = first(c + 1);
+    ITP_LAUNCH(h, ITP_KERNEL_OTHER,
+               (launch_transpose_planes<R, double>(L.psi + (size_t)s0 * N,
+                                                   h->hstage + (size_t)s0 * N,
+                                                   (long long)(s1 - s0) * g.nz, g.nx, g.ny,
+                                                   h->st)));
+    ITP_CUDA(h, cudaEventRecord(ev_out[c], h->st));
+  }
+  ITP_TRY(energies_lane<R>(h, flags));
+  ITP_CUDA(h, cudaMemcpyAsync(h->E_host_pinned, h->E_dev, h->m * sizeof(double),
+                              cudaMemcpyDeviceToHost, h->st));
+  ITP_CUDA(h, cudaMemcpyAsync(h->status_host, h->status, sizeof(int), cudaMemcpyDeviceToHost,
+                              h->st));
+  for (int c = 0; c < C; ++c) {
+    const size_t off = (size_t)first(c) * N, cnt = (size_t)(first(c + 1) - first(c)) * N;
+    ITP_CUDA(h, cudaStreamWaitEvent(h->cst, ev_out[c], 0));
+    ITP_CUDA(h, cudaMemcpyAsync(out + off, h->hstage + off, cnt * sizeof(double),
+                                cudaMemcpyDeviceToHost, h->cst));
+  }
+  ITP_CUDA(h, cudaEventRecord(ev_done, h->cst));
+  ITP_CUDA(h, cudaStreamWaitEvent(h->st, ev_done, 0));
+  return ITP_OK;
+}
+
 }  // namespace
 
 // A batch of independent problems: one handle (and stream) per problem and
@@ -1084,6 +1171,13 @@ void itp_destroy(itp_handle h) {
   cudaFreeHost(h->status_host);
   cudaFreeHost(h->E_host_pinned);
   cudaFree(h->res_dev);
+  if (h->cst) {
+    cudaStreamSynchronize(h->cst);
+    cudaStreamDestroy(h->cst);
+  }
+  cudaFree(h->hstage);
+  for (auto& e : h->hev)
+    if (e) cudaEventDestroy(e);
   for (auto& e : h->prof_events) {
     cudaEventDestroy(e.start);
     cudaEventDestroy(e.stop);
@@ -1280,13 +1374,44 @@ int itp_step(itp_handle h, int order, double tau, int flags, double* E_host) {
   h->launches += h->step_launches;
   h->have_phi = false;
   ITP_CUDA(h, cudaStreamSynchronize(h->st));
-  const int st = *h->status_host;
-  if (st) {
-    ITP_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->st));
-    if (st & 1) return fail(h, ITP_ERR_NOT_PD, "overlap matrix is not positive definite");
-    if (st & 2) return fail(h, ITP_ERR_NOCONV, "Jacobi eigensolver did not converge");
-    if (st & 4) return fail(h, ITP_ERR_TIMEOUT, "a bounded tensor-core pipeline wait expired");
+  ITP_TRY(take_status(h));
+  if (E_host) memcpy(E_host, h->E_host_pinned, h->m * sizeof(double));
+  return ITP_OK;
+}
+
+int itp_step_host(itp_handle h, int order, double tau, int flags, const double* psi_in_host,
+                  double* psi_out_host, double* E_host) {
+  ITP_TRY(check_ready(h, false));
+  if (!psi_in_host || !psi_out_host) return fail(h, ITP_ERR_ARG, "null state buffer");
+  if (order < 2 || order > 2 * kMaxTerms || (order & 1))
+    return fail(h, ITP_ERR_ARG, "order must be even, 2..%d (got %d)", 2 * kMaxTerms, order);
+  if (!(tau > 0) || !std::isfinite(tau)) return fail(h, ITP_ERR_ARG, "tau must be > 0");
+  if (flags != 0 && flags != ITP_RITZ_VALUES)
+    return fail(h, ITP_ERR_ARG, "itp_step_host takes flags 0 or ITP_RITZ_VALUES");
+  const int k = order / 2;
+  const bool mixed = h->precision == ITP_MIXED;
+  // everything allocated or built once, before the first copy is queued
+  if (mixed) {
+    ITP_TRY(step_resources<float>(h, k, tau));
+  } else {
+    ITP_TRY(step_resources<double>(h, k, tau));
   }
+  ITP_TRY(host_step_resources(h));
+  h->have_states = true;   // the lane's states are being replaced
+  h->have_phi = false;
+  h->cur64 = !mixed;
+  const int rc = mixed ? step_host_work<float>(h, k, tau, flags, psi_in_host, psi_out_host)
+                       : step_host_work<double>(h, k, tau, flags, psi_in_host, psi_out_host);
+  // nothing may still read or write the caller's buffers when this returns
+  const cudaError_t e1 = cudaStreamSynchronize(h->cst);
+  const cudaError_t e2 = cudaStreamSynchronize(h->st);
+  if (rc != ITP_OK) {
+    h->have_states = false;   // partly overwritten
+    return rc;
+  }
+  ITP_CUDA(h, e1);
+  ITP_CUDA(h, e2);
+  ITP_TRY(take_status(h));
   if (E_host) memcpy(E_host, h->E_host_pinned, h->m * sizeof(double));
   return ITP_OK;
 }

@@ -47,6 +47,7 @@ SIGNATURES = [
     ("itp_orthonormalize", _I, [_H]),
     ("itp_energies", _I, [_H, _PD, _I]),
     ("itp_step", _I, [_H, _I, _D, _I, _PD]),
+    ("itp_step_host", _I, [_H, _I, _D, _I, _PD, _PD, _PD]),
     ("itp_polish", _I, [_H, _I, _D, _D, _I, ctypes.POINTER(_I), _PD]),
     ("itp_propagate_romberg6", _I, [_H, _D]),
     ("itp_solve_adaptive", _I, [_H, _I, _D, _D, _D, _I, _I, ctypes.POINTER(_I), _PD, _PD, _PD]),
@@ -174,6 +175,31 @@ def itp_energies(h, out: np.ndarray | None, flags: int = ITP_RITZ):
 def itp_step(h, order, tau, flags=ITP_RITZ_VALUES, out: np.ndarray | None = None):
     ptr = None if out is None else out.ctypes.data
     _check(h, load().itp_step(h, int(order), float(tau), int(flags), ptr))
+    return out
+
+
+def _host_buffer(a, count: int, writable: bool) -> int:
+    """Address of a host buffer of `count` doubles: a C-contiguous float64
+    numpy array (checked), or a raw address (int) the caller vouches for."""
+    if isinstance(a, int):
+        return a
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+        raise ValueError("host buffer must be a C-contiguous float64 array")
+    if a.size != count:
+        raise ValueError(f"expected {count} values, got {a.size}")
+    if writable and not a.flags.writeable:
+        raise ValueError("output buffer is read-only")
+    return a.ctypes.data
+
+
+def itp_step_host(h, m, n_points, order, tau, psi_in, psi_out, flags=ITP_RITZ_VALUES,
+                  out: np.ndarray | None = None):
+    """One step between host buffers (itp_step_host): psi_in and psi_out
+    are float64 arrays of m * n_points values (or raw host addresses)."""
+    pin = _host_buffer(psi_in, m * n_points, False)
+    pout = _host_buffer(psi_out, m * n_points, True)
+    ptr = None if out is None else out.ctypes.data
+    _check(h, load().itp_step_host(h, int(order), float(tau), int(flags), pin, pout, ptr))
     return out
 
 
@@ -381,6 +407,17 @@ class ItpGrid:
         ritz=False, diagonal energies)."""
         out = np.empty(self.m, dtype=np.float64)
         return itp_step(self.h, order, tau, ITP_RITZ_VALUES if ritz else 0, out)
+
+    def step_host(self, order, tau, psi_in, psi_out=None, ritz="values"):
+        """One step from host states psi_in to host states psi_out (new
+        array if None), copies overlapped with the device work; returns
+        (psi_out, energies)."""
+        if psi_out is None:
+            psi_out = np.empty((self.m, self.n_points), dtype=np.float64)
+        E = np.empty(self.m, dtype=np.float64)
+        itp_step_host(self.h, self.m, self.n_points, order, tau, psi_in, psi_out,
+                      ITP_RITZ_VALUES if ritz else 0, E)
+        return psi_out, E
 
     def polish(self, order, tau, tol, max_steps):
         out = np.empty(self.m, dtype=np.float64)
