@@ -149,17 +149,18 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_id=None):
-        self.path = tempfile.mktemp(suffix=".csv")
+        self.f = tempfile.NamedTemporaryFile("w", suffix=".csv", delete=False)
+        self.path = self.f.name
         self.proc = None
         cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                "-lms", "200"]
         if gpu_id:
             cmd.insert(1, f"--id={gpu_id}")
         try:
-            self.f = open(self.path, "w")
             self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
-        except Exception:
-            self.proc = None
+        except OSError:   # no nvidia-smi: no clock record
+            self.f.close()
+            os.unlink(self.path)
         self.offset = 0
 
     def begin(self):

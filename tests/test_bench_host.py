@@ -1,0 +1,64 @@
+"""Host logic of bench.py that needs no GPU: the clock sampler keeps only the
+samples taken inside the timed window and reports throttle reasons; it
+degrades to no record when nvidia-smi is absent.  A fake nvidia-smi (a
+shell script writing numbered lines) stands in for the real one."""
+import os
+import stat
+import sys
+import time
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _fake_smi(tmp_path, power_cap="Not Active"):
+    script = tmp_path / "nvidia-smi"
+    script.write_text(
+        "#!/bin/bash\n"
+        "i=0\n"
+        "while true; do\n"
+        f'  echo "0, $((1000+i)), 2070, 500.0, 0x0, Not Active, Not Active, Not Active, {power_cap}"\n'
+        "  i=$((i+1)); sleep 0.05\n"
+        "done\n")
+    script.chmod(script.stat().st_mode | stat.S_IEXEC)
+    return str(tmp_path)
+
+
+def _lines(path):
+    with open(path) as f:
+        return f.read().count("\n")
+
+
+def _wait_lines(path, n, limit=10.0):
+    t0 = time.time()
+    while _lines(path) < n and time.time() - t0 < limit:
+        time.sleep(0.02)
+    assert _lines(path) >= n
+
+
+@pytest.mark.parametrize("cap", ["Not Active", "Active"])
+def test_clock_samples_from_the_window_only(tmp_path, monkeypatch, cap):
+    monkeypatch.setenv("PATH", _fake_smi(tmp_path, cap) + os.pathsep + os.environ["PATH"])
+    c = bench.ClockSampler("GPU-test")
+    assert c.proc is not None
+    _wait_lines(c.path, 3)        # lines 0..2 come before the window
+    c.begin()
+    before = _lines(c.path)
+    _wait_lines(c.path, before + 3)
+    rec = c.stop()
+    assert rec["samples"] >= 3
+    assert rec["sm_mhz"] >= 1000 + before   # nothing from before begin()
+    assert rec["sm_max_mhz"] == 2070.0
+    assert rec["reasons"] == ([] if cap == "Not Active" else ["sw_power_cap"])
+    assert not os.path.exists(c.path)
+
+
+def test_no_nvidia_smi_gives_no_record(tmp_path, monkeypatch):
+    monkeypatch.setenv("PATH", str(tmp_path))   # an empty directory
+    c = bench.ClockSampler(None)
+    c.begin()
+    assert c.stop() is None
