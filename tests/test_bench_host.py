@@ -62,3 +62,51 @@ def test_no_nvidia_smi_gives_no_record(tmp_path, monkeypatch):
     c = bench.ClockSampler(None)
     c.begin()
     assert c.stop() is None
+
+
+class _FakeGrid:
+    """Stands in for ItpGrid: energies approach the oscillator values as
+    2^-steps, returned in descending order (the leg sorts them)."""
+
+    def __init__(self, nx, ny, nz, lx, ly, lz, n_states, n_guard, precision):
+        self.n, self.k, self.closed = n_states, 0, False
+
+    def set_potential(self, V):
+        pass
+
+    def set_states(self, psi):
+        self.k = 0
+
+    def synchronize(self):
+        pass
+
+    def step_graph(self, order, tau):
+        self.k += 1
+        return (bench.ho_closed_shells(self.n) + 0.5 ** self.k)[::-1].copy()
+
+    def close(self):
+        self.closed = True
+
+
+def test_osc32_gpu_leg_logic():
+    import types
+    made = []
+
+    def grid(*a):
+        made.append(_FakeGrid(*a))
+        return made[-1]
+
+    r = bench.osc32_gpu(types.SimpleNamespace(ItpGrid=grid, ITP_FP64=0))
+    assert r["reached"] and r["steps"] == 34   # 2^-34 < 1e-10 <= 2^-33
+    assert made[0].closed
+
+
+def test_steps_to_tol_stops_at_the_limit():
+    steps, err = bench.steps_to_tol(lambda: [2.0], [1.0], 1e-10, 5)
+    assert steps == 5 and err == 1.0
+
+
+def test_osc32_oracle_leg_reaches_the_spectrum():
+    r = bench.osc32_oracle()
+    assert r["reached"] and r["steps"] < bench.OSC32["max_steps"]
+    assert r["max_abs_error_ha"] < 1e-10
