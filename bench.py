@@ -405,6 +405,23 @@ def osc32_oracle():
             "reached": err < c["tol"], "cores": 1}
 
 
+def extrapolate_oracle(cpu, ttt, m):
+    """The oracle's time to tolerance on the 128^3 oscillator, extrapolated
+    (not measured): m states x the FP64 path's step count there, divided by
+    the oracle's measured state-steps per second on the same grid, order and
+    state count.  None when either figure is missing."""
+    if not cpu or not cpu.get("value") or not ttt or "fp64" not in ttt:
+        return None
+    steps = ttt["fp64"].get("fp64_steps")
+    if not steps:
+        return None
+    return {"value_s": round(m * steps / cpu["value"], 1),
+            "how": f"extrapolated, not measured: {m} states x {steps} FP64 steps (the GPU "
+                   "FP64 path's step count to the tolerance on the 128^3 oscillator, same "
+                   "grid, order and state count as the sample) / the oracle's measured "
+                   "state-steps per second"}
+
+
 def adaptive_to_tol(P, precision, tol=1e-8, order=12, n=120, guard=8):
     """The adaptive iteration of Sec. III (itp_solve_adaptive: tau 0.5,
     halved between levels, converged leading states no longer propagated,
@@ -1014,6 +1031,12 @@ def main():
         except Exception:
             cpu = {"value": None, "unit": "state-steps/s", "cores": 1, "kind": "oracle",
                    "sample": "failed: " + (r.stderr.strip().splitlines() or ["?"])[-1]}
+
+    if cpu is not None and ttt is not None:
+        try:
+            ttt["fp64_oracle_extrapolated"] = extrapolate_oracle(cpu, ttt, m)
+        except Exception as ex:   # an auxiliary figure never takes the bench line down
+            ttt["fp64_oracle_extrapolated"] = {"error": f"{type(ex).__name__}: {ex}"}
 
     if rank == 0:
         line = {

@@ -110,3 +110,13 @@ def test_osc32_oracle_leg_reaches_the_spectrum():
     r = bench.osc32_oracle()
     assert r["reached"] and r["steps"] < bench.OSC32["max_steps"]
     assert r["max_abs_error_ha"] < 1e-10
+
+
+def test_oracle_extrapolation():
+    cpu = {"value": 1.1}
+    ttt = {"fp64": {"fp64_steps": 23}}
+    r = bench.extrapolate_oracle(cpu, ttt, 128)
+    assert r["value_s"] == round(128 * 23 / 1.1, 1)
+    assert "not measured" in r["how"]
+    for c, t in ((None, ttt), ({"value": None}, ttt), (cpu, None), (cpu, {"fp64": {}})):
+        assert bench.extrapolate_oracle(c, t, 128) is None
