@@ -120,3 +120,15 @@ def test_oracle_extrapolation():
     assert "not measured" in r["how"]
     for c, t in ((None, ttt), ({"value": None}, ttt), (cpu, None), (cpu, {"fp64": {}})):
         assert bench.extrapolate_oracle(c, t, 128) is None
+
+
+def test_all_cores_oracle_sample_logic():
+    """Spawned single-threaded oracle processes start together and their
+    rates add up (a tiny grid stands in for the workload)."""
+    w = {"n": 16, "box": 8.0, "potential": "ho", "seed": 5, "order": 4, "tau": 0.1}
+    rate, started = bench._cpu_worker((w, time.time() - 1.0, 2))
+    assert rate > 0 and started > 0
+    r = bench.cpu_sample_all_cores(w, steps=2, setup_s=4.0)
+    assert r["cores"] == len(os.sched_getaffinity(0))
+    assert r["value"] > 0 and r["per_core_median"] > 0
+    assert r["start_skew_s"] < 1.0
