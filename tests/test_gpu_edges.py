@@ -1,5 +1,6 @@
 """Edge cases of the state count: a single state (1 x 1 overlap, Cholesky and
-eigenproblem) and the largest block (128 states) in FP64, against the oracle."""
+eigenproblem) and the largest block (128 states), against the oracle; and the
+degenerate block (a zero state: singular overlap, ITP_ERR_NOT_PD)."""
 import numpy as np
 import pytest
 
@@ -38,3 +39,26 @@ def test_state_count_extremes(prec, m):
     assert np.max(np.abs(E - E_ref)) < (1e-11 if prec == "fp64" else 1e-5) * np.max(np.abs(E_ref))
     S = got @ got.T * g.dV
     assert np.max(np.abs(S - np.eye(m))) < (1e-12 if prec == "fp64" else 2e-5)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_zero_state_reports_not_positive_definite(prec):
+    """A state that is zero everywhere makes the overlap matrix singular
+    (first pivot exactly 0): the Cholesky kernel records it, the next
+    synchronising call returns ITP_ERR_NOT_PD, and the handle then steps
+    valid states normally."""
+    g = Grid(16, 16, 8, 8.0, 8.0, 6.0)
+    V = wells_problem(g)
+    psi = seeded_states(g, 3)
+    psi[0] = 0.0
+    with P.ItpGrid(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, 3, 0, PREC[prec]) as h:
+        h.set_potential(V)
+        h.set_states(psi)
+        h.propagate(4, 0.2)
+        h.orthonormalize()
+        with pytest.raises(P.ItpError) as ei:
+            h.energies("values")
+        assert ei.value.code == P.itp.ITP_ERR_NOT_PD
+        h.set_states(seeded_states(g, 3))
+        E = h.step_graph(4, 0.2)
+        assert np.all(np.isfinite(E))
