@@ -1097,8 +1097,10 @@ def main():
                              f"{m * g.n_points * 4 / 1e9:.2f} GB, half spectrum "
                              f"{m * g.nz * g.ny * (g.nx // 2 + 1) * 8 / 1e9:.2f} GB)",
                        "parallelism": f"replicas x{world} (independent problems)",
-                       "timed": "itp_step: each step one CUDA-graph launch (terms of the "
-                                "expansion as parallel branches)"},
+                       "timed": "itp_step: each step one CUDA-graph launch of the whole "
+                                "step's kernels in stream order (the expansion's terms one "
+                                "after another, then the orthonormalisation and the Ritz "
+                                "values)"},
             "gpu_launches": launches,
             "launch_shapes": {"chosen": tuned, "autotune": tune_report},
             "roofline": roof,

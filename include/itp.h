@@ -220,6 +220,21 @@ int itp_solve_adaptive(itp_handle h, int order, double tau0, double reduce, doub
 /* Wait for the handle's stream; returns a pending device status. */
 int itp_synchronize(itp_handle h);
 
+/* Failure-detection test hook (no counterpart in the paper).  Every wait of
+ * the tensor-core kernels of the mixed path (overlap, update, subspace
+ * matrix) on an mbarrier is bounded by one deadline per launch (2 s); when a
+ * wait expires, the kernel stops issuing copies and MMAs, waits at most
+ * 0.1 s for the ones already issued, frees its tensor memory, leaves its
+ * output unwritten and records the timeout, which the next synchronising
+ * call returns as ITP_ERR_TIMEOUT (the states are then unspecified; the
+ * handle stays usable).  This call makes that path run on demand: each of
+ * the handle's next `launches` tensor-core kernel launches made outside a
+ * CUDA-graph capture first waits, before issuing any copy or MMA, on an
+ * mbarrier phase that nothing completes, with a 2 ms limit instead of 2 s.
+ * 0 switches it off.  ITP_FP64 handles launch no tensor-core kernels.
+ * Returns ITP_OK or ITP_ERR_ARG (launches < 0). */
+int itp_test_expire_waits(itp_handle h, int launches);
+
 /* One-line description of the last error on the handle ("" if none); with
  * h == NULL, the reason the calling thread's last itp_create_grid failed
  * (a failed create returns no handle). */
@@ -364,11 +379,13 @@ void itp_batch_destroy(itp_batch_handle b);
  * caller-owned buffers.
  *   phi_device  [m][n_points] doubles on the current device (input, not
  *               modified); any point order, the same for every state
- *   psi_device  [m][n_points] doubles (output); must not overlap phi_device
+ *   psi_device  [m][n_points] doubles (output); its byte range must not
+ *               overlap that of phi_device at all (ITP_ERR_ARG)
  *   m           1..128 states; n_points >= 1; dV > 0 the volume element
  *   cuda_stream the stream to run on (NULL: default stream); the call
  *               synchronises it before returning
- * Returns ITP_OK, ITP_ERR_ARG (bad pointer or size, m > 128),
+ * Returns ITP_OK, ITP_ERR_ARG (bad pointer or size, m > 128, overlapping
+ * buffers),
  * ITP_ERR_NOT_PD (overlap not positive definite; psi_device then holds no
  * meaningful values) or ITP_ERR_CUDA.
  * Scratch space is a fixed array of about 4.3 MiB inside the library, present

@@ -74,6 +74,7 @@ struct itp_grid {
   double* E_host_pinned = nullptr;
   double* res_dev = nullptr;  // [2m] residual norms of the adaptive iteration
   long long launches = 0;
+  int expire_waits = 0;       // test hook: tensor-core launches left that expire their wait
   std::string err;
   bool own_stream = false;    // created by the library (no stream given)
   // CUDA graph of one step (itp_step): propagate + orthonormalize + energies
@@ -154,6 +155,16 @@ void prof_end(itp_handle h, long idx) {
     int r_ = (expr);              \
     if (r_ != ITP_OK) return r_;  \
   } while (0)
+
+// Wait limit for the next tensor-core launch: 0 (the kernels' own launch
+// deadline), or the short limit of the failure-detection test hook
+// (itp_test_expire_waits), which only applies outside a graph capture.
+constexpr unsigned long long kExpireTestNs = 2000000ull;   // 2 ms
+unsigned long long tc_expire(itp_handle h) {
+  if (h->expire_waits <= 0 || h->capturing) return 0;
+  --h->expire_waits;
+  return kExpireTestNs;
+}
 
 bool split_axis(int L, int* r1, int* r2) {
   static const int rad[] = {2, 3, 4, 6, 8, 12, 16};
@@ -434,13 +445,14 @@ int orthonormalize_lane<float>(itp_handle h) {
   Lane<float>& L = h->f32;
   ITP_LAUNCH(h, ITP_KERNEL_GRAM, (launch_tc_gram(L.psi_tmp, L.psi_tmp, h->m,
                                                                h->g.n_points, h->n_chunks_tc,
-                                                               h->partial, h->status, h->st)));
+                                                               h->partial, h->status, h->st,
+                                                               tc_expire(h))));
   ITP_LAUNCH(h, ITP_KERNEL_GRAM_REDUCE,
              launch_gram_reduce(h->partial, h->n_chunks_tc, h->m, h->dV, 1, h->S, h->st));
   ITP_LAUNCH(h, ITP_KERNEL_CHOLESKY, launch_cholesky_inverse(h->S, h->m, h->Mx, h->status, h->st));
   ITP_LAUNCH(h, ITP_KERNEL_APPLY, (launch_tc_apply<float, float>(h->Mx, h->m, L.psi_tmp, L.psi,
                                                                  h->g.n_points, h->status,
-                                                                 h->st)));
+                                                                 h->st, tc_expire(h))));
   return ITP_OK;
 }
 
@@ -493,7 +505,7 @@ int energies_lane(itp_handle h, int flags) {
                                        reinterpret_cast<const float*>(L.psi),
                                        reinterpret_cast<const float*>(L.psi_tmp), h->m,
                                        g.n_points, h->n_chunks_tc, h->partial, h->status,
-                                       h->st)));
+                                       h->st, tc_expire(h))));
   } else {
     ITP_LAUNCH(h, ITP_KERNEL_GRAM, (launch_gram_partial<double, double, double>(
                                        reinterpret_cast<const double*>(L.psi), h->acc, h->m,
@@ -508,7 +520,7 @@ int energies_lane(itp_handle h, int flags) {
       ITP_LAUNCH(h, ITP_KERNEL_APPLY, (launch_tc_apply<float, float>(
                                           h->Mx, h->m, reinterpret_cast<const float*>(L.psi),
                                           reinterpret_cast<float*>(L.psi_tmp), g.n_points,
-                                          h->status, h->st)));
+                                          h->status, h->st, tc_expire(h))));
     } else {
       ITP_LAUNCH(h, ITP_KERNEL_APPLY, (launch_apply_matrix<double, double>(
                                           h->Mx, h->m, 0, reinterpret_cast<const double*>(L.psi),
@@ -532,9 +544,10 @@ int take_status(itp_handle h) {
   const int s = *h->status_host;
   if (s) {
     ITP_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->st));
+    // an expired wait left outputs unwritten, so later flags may follow from it
+    if (s & 4) return fail(h, ITP_ERR_TIMEOUT, "a bounded tensor-core pipeline wait expired");
     if (s & 1) return fail(h, ITP_ERR_NOT_PD, "overlap matrix is not positive definite");
     if (s & 2) return fail(h, ITP_ERR_NOCONV, "Jacobi eigensolver did not converge");
-    if (s & 4) return fail(h, ITP_ERR_TIMEOUT, "a bounded tensor-core pipeline wait expired");
   }
   return ITP_OK;
 }
@@ -1446,6 +1459,13 @@ int itp_polish(itp_handle h, int order, double tau, double tol, int max_steps, i
   ITP_TRY(do_energies(h, nullptr, ITP_RITZ));
   if (steps_out) *steps_out = step;
   if (E_host) memcpy(E_host, cur.data(), h->m * sizeof(double));
+  return ITP_OK;
+}
+
+int itp_test_expire_waits(itp_handle h, int launches) {
+  if (!h) return ITP_ERR_ARG;
+  if (launches < 0) return fail(h, ITP_ERR_ARG, "launch count must be >= 0");
+  h->expire_waits = launches;
   return ITP_OK;
 }
 

@@ -171,14 +171,18 @@ template <typename TX, typename TY>
 cudaError_t launch_apply_matrix(const double* M, int m, int lower, const TX* X, TY* Y,
                                 long long n_points, cudaStream_t st);
 // Tensor-core (tcgen05 TF32, 3xTF32 split) versions, m <= 128; status gets
-// bit 4 if a bounded mbarrier wait expired.
+// bit 4 if a bounded mbarrier wait expired (the kernel then leaves its
+// output unwritten).  expire_ns != 0 is the failure-detection test hook:
+// every CTA first waits, with that limit and before issuing any copy or
+// MMA, on an mbarrier phase that nothing completes.
 // Gram: FP32 operands (16-byte aligned, n_points % 8 == 0) streamed in by
 // bulk copies; A == B computes A A^T with one operand tile per step.
 cudaError_t launch_tc_gram(const float* A, const float* B, int m, long long n_points,
-                           int n_chunks, double* partial, int* status, cudaStream_t st);
+                           int n_chunks, double* partial, int* status, cudaStream_t st,
+                           unsigned long long expire_ns = 0);
 template <typename TX, typename TY>
 cudaError_t launch_tc_apply(const double* M, int m, const TX* X, TY* Y, long long n_points,
-                            int* status, cudaStream_t st);
+                            int* status, cudaStream_t st, unsigned long long expire_ns = 0);
 // Precision conversion of whole state blocks.
 template <typename TS, typename TD>
 cudaError_t launch_convert(const TS* src, TD* dst, long long count, cudaStream_t st);

@@ -9,6 +9,8 @@
 // (kNoallocBytes) until the process exits.
 #include <cuda_runtime.h>
 
+#include <stdint.h>
+
 #include <mutex>
 
 #include "itp.h"
@@ -51,9 +53,15 @@ cudaError_t scratch_address(void** out) {
 
 extern "C" int itp_orthonormalize_noalloc(const double* phi_device, double* psi_device, int m,
                                           long long n_points, double dV, void* cuda_stream) {
-  if (!phi_device || !psi_device || m < 1 || m > kNoallocMaxM || n_points < 1 || !(dV > 0) ||
-      (const void*)phi_device == (const void*)psi_device)
+  if (!phi_device || !psi_device || m < 1 || m > kNoallocMaxM || n_points < 1 ||
+      n_points > (1LL << 48) || !(dV > 0))
     return ITP_ERR_ARG;
+  // psi = L^{-1} phi is written while other CTAs still read phi: the two
+  // byte ranges must be disjoint, not merely start at different addresses
+  const uintptr_t bytes = (uintptr_t)m * (uintptr_t)n_points * sizeof(double);
+  const uintptr_t a0 = reinterpret_cast<uintptr_t>(phi_device);
+  const uintptr_t b0 = reinterpret_cast<uintptr_t>(psi_device);
+  if (a0 < b0 + bytes && b0 < a0 + bytes) return ITP_ERR_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   void* base = nullptr;
   if (scratch_address(&base) != cudaSuccess) return ITP_ERR_CUDA;

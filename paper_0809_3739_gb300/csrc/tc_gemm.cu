@@ -17,8 +17,13 @@
 // descriptor's leading byte offset (next core matrix along K) is 128 and its
 // stride byte offset (next 8-row group) is KC*128.
 //
-// Every wait on an mbarrier is bounded; on expiry the kernel records
-// ITP status bit 4 and carries on, so no launch can hang.
+// Every wait on an mbarrier is bounded by one deadline per launch, taken at
+// kernel start.  When a wait expires, the CTA agrees on it at its next block
+// barrier (__syncthreads_or), issues no further copy or MMA, waits a short
+// bounded time for the copies and MMAs it has already issued, frees its
+// TMEM, leaves its outputs unwritten and records ITP status bit 4; the host
+// reports ITP_ERR_TIMEOUT.  A launch therefore ends within the deadline plus
+// the drain limit.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
@@ -33,7 +38,8 @@ namespace itp {
 namespace {
 
 constexpr int kTcThreads = 256;
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s per wait at most
+constexpr unsigned long long kLaunchLimitNs = 2000000000ull;  // 2 s per launch at most
+constexpr unsigned long long kDrainLimitNs = 100000000ull;    // 0.1 s per in-flight operation
 constexpr int kStatusTimeout = 4;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -65,17 +71,22 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Bounded wait for the phase with the given parity to complete: gives up
-// after kWaitLimitNs, records the timeout in the status word and returns.
-__device__ __forceinline__ void mbar_wait(uint64_t* bar, uint32_t parity, int* status) {
-  if (mbar_try_wait(bar, parity)) return;
-  const unsigned long long t0 = global_ns();
+// Bounded wait for the phase with the given parity to complete: true once it
+// has, false if the deadline (a %globaltimer value) passed first.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          unsigned long long deadline) {
   while (!mbar_try_wait(bar, parity)) {
-    if (global_ns() - t0 > kWaitLimitNs) {
-      atomicOr(status, kStatusTimeout);
-      return;
-    }
+    if (global_ns() > deadline) return false;
   }
+  return true;
+}
+
+// After an expired wait: one thread waits, each for at most kDrainLimitNs,
+// for an operation the CTA issued earlier (a TMA copy or an MMA commit
+// signalling the mbarrier phase of that parity), so that nothing writes the
+// CTA's shared memory or TMEM after it has left them.
+__device__ __forceinline__ void drain_wait(uint64_t* bar, uint32_t parity) {
+  mbar_wait(bar, parity, global_ns() + kDrainLimitNs);
 }
 
 __device__ __forceinline__ void fence_barrier_init() {
@@ -221,7 +232,7 @@ template <bool SAME>
 __global__ void __launch_bounds__(kTcThreads, 1)
     tc_gram_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    int m, long long N, long long chunk, double* __restrict__ partial,
-                   int* status) {
+                   int* status, unsigned long long expire_ns) {
   constexpr int NOPS = SAME ? 1 : 2;                // operands per tile
   constexpr int RAW = SAME ? 4 : 3;                 // raw ring depth
   extern __shared__ __align__(1024) unsigned char smraw[];
@@ -237,6 +248,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   auto raw = [&](int r, int op) { return sbase + raw_off + (uint32_t)((r * NOPS + op) * kRawBytes); };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // one deadline for the whole launch (expire_ns != 0: the test hook's short limit)
+  const unsigned long long deadline = global_ns() + (expire_ns ? expire_ns : kLaunchLimitNs);
   if (threadIdx.x == 0) {
     for (int r = 0; r < RAW; ++r) mbar_init(&full[r], 1);
     mbar_init(&mma_done[0], 1);
@@ -248,6 +261,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
+  // Test hook: before any copy or MMA is issued, wait on a phase that nothing
+  // completes (no copy has been issued on full[0] yet); it expires after
+  // expire_ns and the CTA takes the abort path with nothing in flight.
+  bool ok = expire_ns ? mbar_wait(&full[0], 0u, deadline) : true;
 
   // warp w reads TMEM lane quadrant w % 4; warps 4.. take the upper column halves
   const int quad = warp & 3, chalf = warp >> 2;
@@ -275,18 +292,27 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tma_load_2d(raw(r, 0), &tmA, x, 0, &full[r]);
     if (!SAME) tma_load_2d(raw(r, 1), &tmB, x, 0, &full[r]);
   };
-  if (threadIdx.x == 0)
-    for (int t = 0; t < RAW && t < ntiles; ++t) issue(t, t);
+  // tiles [0, issued) have their copies issued, [0, committed) their MMAs
+  int issued = 0, committed = 0, t_stop = 0;
+  bool aborted = __syncthreads_or(!ok) != 0;
+  if (!aborted) {
+    issued = RAW < ntiles ? RAW : ntiles;
+    if (threadIdx.x == 0)
+      for (int t = 0; t < issued; ++t) issue(t, t);
+  }
 
   constexpr uint32_t idesc = idesc_tf32(128, 128);
   const uint32_t sbo = kGramKC * 128;
-  for (int t = 0; t < ntiles; ++t) {
+  for (int t = 0; t < ntiles && !aborted; ++t) {
     const int r = t % RAW, c = t & 1;
-    mbar_wait(&full[r], (uint32_t)((t / RAW) & 1), status);
+    ok = mbar_wait(&full[r], (uint32_t)((t / RAW) & 1), deadline);
     if (t >= 2) {   // tile t-2 is done: its stage and accumulator are free
-      mbar_wait(&mma_done[c], (uint32_t)(((t - 2) >> 1) & 1), status);
-      tc_fence_after();
-      drain(c);
+      if (ok) ok = mbar_wait(&mma_done[c], (uint32_t)(((t - 2) >> 1) & 1), deadline);
+      // TMEM loads are warp-collective: the warp drains only if all its lanes saw the MMA end
+      if (__all_sync(0xffffffffu, ok)) {
+        tc_fence_after();
+        drain(c);
+      }
     }
 #pragma unroll
     for (int op = 0; op < NOPS; ++op) {
@@ -310,7 +336,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     fence_async_smem();
     tc_fence_before();
-    __syncthreads();
+    if (__syncthreads_or(!ok)) {   // a wait expired somewhere in the CTA
+      aborted = true;
+      t_stop = t;
+      break;
+    }
+    committed = t + 1;
+    if (t + RAW < ntiles) issued = t + RAW + 1;
     if (threadIdx.x == 0) {
       tc_fence_after();
       const uint32_t ahi = canon(c, 0, 0), alo = canon(c, 0, 1);
@@ -332,19 +364,39 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (t + RAW < ntiles) issue(t + RAW, r);
     }
   }
-  // the last two tiles are not drained yet
-  for (int tl = ntiles >= 2 ? ntiles - 2 : 0; tl < ntiles; ++tl) {
-    mbar_wait(&mma_done[tl & 1], (uint32_t)((tl >> 1) & 1), status);
-    tc_fence_after();
-    drain(tl & 1);
+  if (!aborted) {
+    // the last two tiles are not drained yet
+    ok = true;
+    for (int tl = ntiles >= 2 ? ntiles - 2 : 0; tl < ntiles; ++tl) {
+      if (ok) ok = mbar_wait(&mma_done[tl & 1], (uint32_t)((tl >> 1) & 1), deadline);
+      if (__all_sync(0xffffffffu, ok)) {
+        tc_fence_after();
+        drain(tl & 1);
+      }
+    }
+    if (__syncthreads_or(!ok)) {
+      aborted = true;
+      t_stop = ntiles;
+    }
   }
-  double* out = partial + (long long)blockIdx.x * m * m;
-  const int i = quad * 32 + lane;
-  if (i < m) {
+  if (aborted) {
+    // wait (bounded) for what is still in flight: the copies of tiles
+    // [t_stop, issued) and the MMAs of the last two committed tiles
+    if (threadIdx.x == 0) {
+      atomicOr(status, kStatusTimeout);
+      for (int t = t_stop; t < issued; ++t) drain_wait(&full[t % RAW], (uint32_t)((t / RAW) & 1));
+      for (int t = committed >= 2 ? committed - 2 : 0; t < committed; ++t)
+        drain_wait(&mma_done[t & 1], (uint32_t)((t >> 1) & 1));
+    }
+  } else {
+    double* out = partial + (long long)blockIdx.x * m * m;
+    const int i = quad * 32 + lane;
+    if (i < m) {
 #pragma unroll
-    for (int q = 0; q < 64; ++q) {
-      const int j = chalf * 64 + q;
-      if (j < m) out[(long long)i * m + j] = (double)acc[q];
+      for (int q = 0; q < 64; ++q) {
+        const int j = chalf * 64 + q;
+        if (j < m) out[(long long)i * m + j] = (double)acc[q];
+      }
     }
   }
   tc_fence_before();
@@ -438,13 +490,17 @@ __device__ __forceinline__ void store_points(const float (&v)[4][4], uint32_t hi
 }
 
 // Epilogue of one finished tile: TMEM -> shared (warps 0..3, one lane
-// quadrant each) -> coalesced 16-byte global stores by all threads.
+// quadrant each) -> coalesced 16-byte global stores by all threads.  ok:
+// this thread saw the tile's MMAs complete; if any thread of the CTA did
+// not, nothing is stored and false is returned (CTA-uniform).
 template <typename TY>
-__device__ __forceinline__ void apply_epilogue(uint32_t tmem_col, float* stage, int m,
-                                               TY* __restrict__ Y, long long N, long long p0) {
+__device__ __forceinline__ bool apply_epilogue(uint32_t tmem_col, float* stage, int m,
+                                               TY* __restrict__ Y, long long N, long long p0,
+                                               bool ok) {
   constexpr int NT = 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (warp < 4) {
+  // TMEM loads are warp-collective: a warp loads only if all its lanes saw the MMAs end
+  if (warp < 4 && __all_sync(0xffffffffu, ok)) {
     uint32_t r[32];
     tmem_ld32(tmem_col + ((uint32_t)(warp * 32) << 16), r);
     float* row = stage + (warp * 32 + lane) * (NT + 4);
@@ -455,7 +511,7 @@ __device__ __forceinline__ void apply_epilogue(uint32_t tmem_col, float* stage, 
                       __uint_as_float(r[q + 2]), __uint_as_float(r[q + 3]));
   }
   tc_fence_before();
-  __syncthreads();
+  if (__syncthreads_or(!ok)) return false;
   // 128 rows x 8 float4 per row
   for (int L = threadIdx.x; L < 128 * (NT / 4); L += kTcThreads) {
     const int i = L >> 3, c4 = L & 7;
@@ -471,12 +527,13 @@ __device__ __forceinline__ void apply_epilogue(uint32_t tmem_col, float* stage, 
         if (p + q < N) dst[q] = w[q];
     }
   }
+  return true;
 }
 
 template <typename TX, typename TY>
 __global__ void __launch_bounds__(kTcThreads, 1)
     tc_apply_kernel(const double* __restrict__ Mg, int m, const TX* __restrict__ X,
-                    TY* __restrict__ Y, long long N, int* status) {
+                    TY* __restrict__ Y, long long N, int* status, unsigned long long expire_ns) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ uint32_t tmem_base;
@@ -486,6 +543,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     return sbase + 2u * kMBytes + (uint32_t)((s * 2 + which) * kXTileBytes);
   };
   float* ostage = reinterpret_cast<float*>(smraw + 2 * kMBytes + 4 * kXTileBytes);
+  // one deadline for the whole launch (expire_ns != 0: the test hook's short limit)
+  const unsigned long long deadline = global_ns() + (expire_ns ? expire_ns : kLaunchLimitNs);
 
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
@@ -523,17 +582,35 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const long long ntiles = (N + kApplyNT - 1) / kApplyNT;
   int local = 0;
   long long prev_tile = -1;
+  // bit s: an MMA commit on bar[s] not yet seen complete; its phase parity
+  uint32_t pending = 0u, pend_parity = 0u;
+  // Test hook: before any MMA is issued, wait on a phase that nothing
+  // completes (no commit has been made on bar[0] yet); it expires after
+  // expire_ns and the CTA takes the abort path with nothing in flight.
+  bool ok = expire_ns ? mbar_wait(&bar[0], 0u, deadline) : true;
+  bool aborted = __syncthreads_or(!ok) != 0;
   float cur[4][4], nxt[4][4];
-  if ((long long)blockIdx.x < ntiles) load_points(X, m, N, (long long)blockIdx.x * kApplyNT, cur);
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++local) {
+  if ((long long)blockIdx.x < ntiles && !aborted)
+    load_points(X, m, N, (long long)blockIdx.x * kApplyNT, cur);
+  for (long long tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x, ++local) {
     const int s = local & 1;
-    if (local >= 2) mbar_wait(&bar[s], (uint32_t)(((local - 2) >> 1) & 1), status);
+    ok = true;
+    if (local >= 2) {
+      ok = mbar_wait(&bar[s], (uint32_t)(((local - 2) >> 1) & 1), deadline);
+      pending &= ~(1u << s);   // settled: complete, or drained below
+    }
     store_points(cur, xpart(s, 0), xpart(s, 1));
     const long long next = tile + gridDim.x;
     if (next < ntiles) load_points(X, m, N, next * kApplyNT, nxt);   // in flight meanwhile
     fence_async_smem();
     tc_fence_before();
-    __syncthreads();
+    if (__syncthreads_or(!ok)) {   // a wait expired somewhere in the CTA
+      pending |= 1u << s;          // tile local-2's MMAs may still run
+      aborted = true;
+      break;
+    }
+    pending |= 1u << s;
+    pend_parity = (pend_parity & ~(1u << s)) | ((uint32_t)((local >> 1) & 1) << s);
     if (threadIdx.x == 0) {
       tc_fence_after();
       const uint32_t d = tmem + (uint32_t)(s * kApplyNT);
@@ -553,9 +630,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // epilogue of the previous tile (its MMAs ran while this tile staged)
     if (prev_tile >= 0) {
       const int ps = (local - 1) & 1;
-      mbar_wait(&bar[ps], (uint32_t)(((local - 1) >> 1) & 1), status);
+      ok = mbar_wait(&bar[ps], (uint32_t)(((local - 1) >> 1) & 1), deadline);
       tc_fence_after();
-      apply_epilogue(tmem + (uint32_t)(ps * kApplyNT), ostage, m, Y, N, prev_tile * kApplyNT);
+      if (!apply_epilogue(tmem + (uint32_t)(ps * kApplyNT), ostage, m, Y, N,
+                          prev_tile * kApplyNT, ok)) {
+        aborted = true;
+        break;
+      }
+      pending &= ~(1u << ps);
     }
     prev_tile = tile;
 #pragma unroll
@@ -563,11 +645,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
       for (int q = 0; q < 4; ++q) cur[e][q] = nxt[e][q];
   }
-  if (prev_tile >= 0) {
+  if (prev_tile >= 0 && !aborted) {
     const int ps = (local - 1) & 1;
-    mbar_wait(&bar[ps], (uint32_t)(((local - 1) >> 1) & 1), status);
+    ok = mbar_wait(&bar[ps], (uint32_t)(((local - 1) >> 1) & 1), deadline);
     tc_fence_after();
-    apply_epilogue(tmem + (uint32_t)(ps * kApplyNT), ostage, m, Y, N, prev_tile * kApplyNT);
+    if (apply_epilogue(tmem + (uint32_t)(ps * kApplyNT), ostage, m, Y, N, prev_tile * kApplyNT,
+                       ok))
+      pending &= ~(1u << ps);
+    else
+      aborted = true;
+  }
+  if (aborted && threadIdx.x == 0) {
+    // wait (bounded) for the MMAs still in flight before TMEM is freed
+    atomicOr(status, kStatusTimeout);
+    for (int b = 0; b < 2; ++b)
+      if ((pending >> b) & 1u) drain_wait(&bar[b], (pend_parity >> b) & 1u);
   }
   tc_fence_before();
   __syncthreads();
@@ -580,7 +672,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }  // namespace
 
 cudaError_t launch_tc_gram(const float* A, const float* B, int m, long long n_points,
-                           int n_chunks, double* partial, int* status, cudaStream_t st) {
+                           int n_chunks, double* partial, int* status, cudaStream_t st,
+                           unsigned long long expire_ns) {
   if (m > 128 || m < 1 || (n_points % 8) || n_points >= (1LL << 31)) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15)
     return cudaErrorInvalidValue;
@@ -598,20 +691,20 @@ cudaError_t launch_tc_gram(const float* A, const float* B, int m, long long n_po
                              (int)smem);
     if (e != cudaSuccess) return e;
     tc_gram_kernel<true><<<n_chunks, kTcThreads, smem, st>>>(tmA, tmB, m, n_points, chunk,
-                                                             partial, status);
+                                                             partial, status, expire_ns);
   } else {
     e = cudaFuncSetAttribute(tc_gram_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
     tc_gram_kernel<false><<<n_chunks, kTcThreads, smem, st>>>(tmA, tmB, m, n_points, chunk,
-                                                              partial, status);
+                                                              partial, status, expire_ns);
   }
   return cudaGetLastError();
 }
 
 template <typename TX, typename TY>
 cudaError_t launch_tc_apply(const double* M, int m, const TX* X, TY* Y, long long n_points,
-                            int* status, cudaStream_t st) {
+                            int* status, cudaStream_t st, unsigned long long expire_ns) {
   if (m > 128 || m < 1) return cudaErrorInvalidValue;
   // M hi/lo 128 KB, two X stages 64 KB, output staging 18 KB
   const size_t smem = 2 * (size_t)kMBytes + 4 * (size_t)kXTileBytes + 128 * (kApplyNT + 4) * 4;
@@ -623,11 +716,13 @@ cudaError_t launch_tc_apply(const double* M, int m, const TX* X, TY* Y, long lon
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long long ntiles = (n_points + kApplyNT - 1) / kApplyNT;
   const int blocks = (int)(ntiles < sms ? ntiles : sms);
-  tc_apply_kernel<TX, TY><<<blocks, kTcThreads, smem, st>>>(M, m, X, Y, n_points, status);
+  tc_apply_kernel<TX, TY><<<blocks, kTcThreads, smem, st>>>(M, m, X, Y, n_points, status,
+                                                             expire_ns);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_tc_apply<float, float>(const double*, int, const float*, float*,
-                                                   long long, int*, cudaStream_t);
+                                                   long long, int*, cudaStream_t,
+                                                   unsigned long long);
 
 }  // namespace itp

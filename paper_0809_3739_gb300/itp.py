@@ -52,6 +52,7 @@ SIGNATURES = [
     ("itp_propagate_romberg6", _I, [_H, _D]),
     ("itp_solve_adaptive", _I, [_H, _I, _D, _D, _D, _I, _I, ctypes.POINTER(_I), _PD, _PD, _PD]),
     ("itp_synchronize", _I, [_H]),
+    ("itp_test_expire_waits", _I, [_H, _I]),
     ("itp_last_error", ctypes.c_char_p, [_H]),
     ("itp_kernel_launches", ctypes.c_longlong, [_H]),
     ("itp_profile", _I, [_H, _I]),
@@ -228,6 +229,10 @@ def itp_solve_adaptive(h, m, order, tau0, reduce, gamma, max_steps=200, max_leve
 
 def itp_synchronize(h):
     _check(h, load().itp_synchronize(h))
+
+
+def itp_test_expire_waits(h, launches: int):
+    _check(h, load().itp_test_expire_waits(h, int(launches)))
 
 
 def itp_last_error(h) -> str:
@@ -426,6 +431,9 @@ class ItpGrid:
 
     def synchronize(self):
         itp_synchronize(self.h)
+
+    def test_expire_waits(self, launches):
+        itp_test_expire_waits(self.h, launches)
 
     def solve_adaptive(self, order, tau0, reduce, gamma, max_steps=200, max_levels=12):
         return itp_solve_adaptive(self.h, self.m, order, tau0, reduce, gamma, max_steps,

@@ -40,3 +40,9 @@ def wells_problem(g: Grid, n_wells: int = 5, seed: int = 3):
 
 def seeded_states(g: Grid, m: int, seed: int = 1234):
     return normal_states(m, g.n_points, seed)
+
+
+def report(name: str, err: float, tol: float) -> None:
+    """Print an observed error beside its bound (shown with pytest -s), so
+    that every parity check leaves the margin it passed with on record."""
+    print(f"[parity] {name}: err={err:.3e} tol={tol:.3e} err/tol={err / tol:.3g}", flush=True)

@@ -62,3 +62,47 @@ def test_zero_state_reports_not_positive_definite(prec):
         h.set_states(seeded_states(g, 3))
         E = h.step_graph(4, 0.2)
         assert np.all(np.isfinite(E))
+
+
+@pytest.mark.parametrize("which", ["overlap", "update", "subspace"])
+def test_expired_wait_reports_timeout_and_handle_recovers(which):
+    """The bounded-wait expiry path of the tensor-core kernels, made to run
+    without any fault: itp_test_expire_waits makes a launch wait, before it
+    issues any copy or MMA, on an mbarrier phase nothing completes, with a
+    2 ms limit.  The kernel leaves its output unwritten, frees its tensor
+    memory and records the timeout; the next synchronising call returns
+    ITP_ERR_TIMEOUT, and the same handle then steps normally and matches the
+    oracle."""
+    g = Grid(16, 16, 8, 8.0, 8.0, 6.0)
+    V = wells_problem(g)
+    m = 4
+    psi = seeded_states(g, m)
+    with P.ItpGrid(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, m, 0, P.ITP_MIXED) as h:
+        h.set_potential(V)
+        h.set_states(psi)
+        h.propagate(4, 0.2)
+        if which == "overlap":        # the first tensor-core launch: the overlap Gram
+            h.test_expire_waits(1)
+            h.orthonormalize()
+        elif which == "update":       # the second: psi = L^{-1} phi
+            h.orthonormalize()        # (queued, not synchronised)
+            h.synchronize()
+            h.set_states(psi)
+            h.propagate(4, 0.2)
+            h.test_expire_waits(2)
+            h.orthonormalize()        # Gram expires, then the update
+        else:                         # the subspace matrix of the energies
+            h.orthonormalize()
+            h.synchronize()
+            h.test_expire_waits(1)
+        with pytest.raises(P.ItpError) as ei:
+            h.energies("values")
+        assert ei.value.code == P.itp.ITP_ERR_TIMEOUT
+        assert "expired" in P.itp_last_error(h.h)
+        # the hook is spent; the handle is usable and correct again
+        h.set_states(psi)
+        ref = psi.copy()
+        for _ in range(2):
+            E = h.step_graph(4, 0.2)
+            ref, E_ref = O.itp_step(ref, V, g, 4, 0.2)
+            assert np.max(np.abs(E - E_ref)) < 1e-5 * np.max(np.abs(E_ref))

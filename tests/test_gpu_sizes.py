@@ -1,0 +1,195 @@
+"""Oracle parity of every compile-time specialised FFT pass.
+
+The plane and pencil passes are instantiated per edge length (the index
+arithmetic of a 128 x 128 plane or a 128-long, 33-column pencil folds to
+constants), so each instantiation is a separate piece of code that needs its
+own comparison with the oracle.  These tests run the cubic grids whose
+passes are specialised -- 48^3, 64^3, 96^3 and the 128^3 C60-like workload
+itself -- in both precisions through propagation at order 12 (forward,
+merged, final/term passes and both pencil modes), orthonormalisation, and
+the energies (the H psi plane pass and the kinetic pencil), and force every
+launch shape the autotuner may pick on the 96^3 and 128^3 grids: each
+pencil width it tries and each plane form.  Every element is compared.
+The observed errors are printed beside their bounds.
+"""
+import numpy as np
+import pytest
+
+from itp_workloads import Grid, c60_like_potential, cubic
+from oracle import itp_oracle as O
+
+from gpu_helpers import propagate_tolerance, report, seeded_states, wells_problem
+
+pytestmark = pytest.mark.gpu
+
+import paper_0809_3739_gb300 as P  # noqa: E402  (fails loudly without libitp.so)
+
+PREC = {"fp64": P.ITP_FP64, "mixed": P.ITP_MIXED}
+RB = {"fp64": 8, "mixed": 4}
+# orthonormalised states and energies (relative), as in the other parity tests
+STATE_TOL = {"fp64": 1e-11, "mixed": 2e-4}
+ENERGY_TOL = {"fp64": 1e-11, "mixed": 1e-5}
+
+
+def _relerr(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def _problem(edge):
+    """Cubic grids with specialised passes.  96^3 and 128^3 carry the
+    C60-like well in the 32 bohr box of the headline workload; the smaller
+    ones a few Gaussian wells."""
+    if edge >= 96:
+        g = cubic(edge, 32.0)
+        return g, c60_like_potential(g)
+    g = cubic(edge, 16.0)
+    return g, wells_problem(g)
+
+
+def _row_pitch(nx):
+    p = nx + nx // 16 + 2
+    return p if p % 2 else p + 1
+
+
+def _plane_forms(g, prec):
+    """(split, row_tb) forms valid for the grid (the rules of itp.h)."""
+    rb = RB[prec]
+    whole = ((g.ny // 2) * _row_pitch(g.nx) + g.nx + g.ny) * 2 * rb <= 227 * 1024
+    out = [(0, 0)] if whole else []
+    for tb in (32, 16, 8):
+        if ((g.ny // 2) % tb == 0 and (tb * _row_pitch(g.nx) + g.nx) * 2 * rb <= 96 * 1024
+                and (tb != 32 or (prec == "mixed" and g.nx == 256))):
+            out.append((1, tb))
+    return out
+
+
+def _pencil_widths(g):
+    """The widths itp_autotune tries: nx/2+1 columns cut into 1..4 blocks."""
+    nxh = g.nx // 2 + 1
+    return sorted({-(-nxh // c) for c in (1, 2, 3, 4)}, reverse=True)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("edge", [48, 64, 96, 128])
+def test_cubic_step_matches_oracle(edge, prec):
+    """Propagation at order 12 (all five plane-pass kinds and the
+    propagating pencil), Cholesky orthonormalisation, and energies with and
+    without the Ritz step (H psi plane pass, kinetic pencil) on the default
+    launch shapes, every element against the oracle."""
+    g, V = _problem(edge)
+    m = 3
+    psi = seeded_states(g, m)
+    order, tau = 12, 0.25
+    with P.ItpGrid(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, m, 0, PREC[prec]) as h:
+        h.set_potential(V)
+        h.set_states(psi)
+        shape = h.get_tuning()
+        h.propagate(order, tau)
+        phi = h.get_phi()
+        h.orthonormalize()
+        got = h.get_states()
+        E_diag = h.energies(False)
+        E_ritz = h.energies("values")
+    phi_ref = O.propagate(psi, V, g, order, tau)
+    tol = propagate_tolerance(order, g.n_points, prec)
+    err = _relerr(phi, phi_ref)
+    report(f"{edge}^3 {prec} propagate order {order} {shape}", err, tol)
+    assert err < tol
+    psi_ref, _ = O.cholesky_orthonormalize(phi_ref, g.dV)
+    err = _relerr(got, psi_ref)
+    report(f"{edge}^3 {prec} orthonormalize", err, STATE_TOL[prec])
+    assert err < STATE_TOL[prec]
+    # energies of the states the GPU holds (the oracle's own orthonormal
+    # states differ from them by the propagation error above)
+    E_ref, _, _ = O.energies(got, V, g, ritz=False)
+    err = float(np.max(np.abs(E_diag - E_ref)) / np.max(np.abs(E_ref)))
+    report(f"{edge}^3 {prec} energies (psi|H|psi)", err, ENERGY_TOL[prec])
+    assert err < ENERGY_TOL[prec]
+    E_ref, _, _ = O.energies(got, V, g, ritz=True)
+    err = float(np.max(np.abs(E_ritz - E_ref)) / np.max(np.abs(E_ref)))
+    report(f"{edge}^3 {prec} Ritz values", err, ENERGY_TOL[prec])
+    assert err < ENERGY_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("edge", [96, 128])
+def test_every_launch_shape_at_full_edge(edge, prec):
+    """Every (plane form, pencil width) the autotuner may pick on the 96^3
+    and 128^3 grids -- the specialised 65- and 33-column pencils at 128, the
+    49- and 25-column ones at 96, the generic ones in between, whole planes
+    and row + column passes -- gives the oracle's propagation (order 4:
+    forward, merged, final passes) and energies (H psi, kinetic pencil)."""
+    g, V = _problem(edge)
+    m = 2
+    psi = seeded_states(g, m, seed=77)
+    order, tau = 4, 0.3
+    phi_ref = O.propagate(psi, V, g, order, tau)
+    psi0, _ = O.cholesky_orthonormalize(psi, g.dV)
+    E_ref, _, _ = O.energies(psi0, V, g, ritz=False)
+    tol = propagate_tolerance(order, g.n_points, prec)
+    with P.ItpGrid(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, m, 0, PREC[prec]) as h:
+        h.set_potential(V)
+        gram = h.get_tuning()["gram_ctas"]
+        for split, tb in _plane_forms(g, prec):
+            for w in _pencil_widths(g):
+                try:
+                    h.set_tuning(w, split, tb, gram)
+                except P.ItpError:
+                    continue   # e.g. an FP64 pencil slab over the shared-memory limit
+                h.set_states(psi)
+                h.propagate(order, tau)
+                phi = h.get_phi()
+                err = _relerr(phi, phi_ref)
+                report(f"{edge}^3 {prec} propagate split={split} tb={tb} w={w}", err, tol)
+                assert err < tol, (split, tb, w)
+                h.set_states(psi0)
+                E = h.energies(False)
+                err = float(np.max(np.abs(E - E_ref)) / np.max(np.abs(E_ref)))
+                report(f"{edge}^3 {prec} energies split={split} tb={tb} w={w}", err,
+                       ENERGY_TOL[prec])
+                assert err < ENERGY_TOL[prec], (split, tb, w)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_graph_steps_at_128_match_oracle(prec):
+    """The headline's timed form -- itp_step graph replays at 128^3, order
+    12, Ritz values -- against the oracle's iterations, two steps, after the
+    autotuner has picked the launch shapes."""
+    g, V = _problem(128)
+    m = 3
+    psi = seeded_states(g, m, seed=5)
+    with P.ItpGrid(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, m, 0, PREC[prec]) as h:
+        h.set_potential(V)
+        h.set_states(psi)
+        chosen, _ = h.autotune(12, 0.25)
+        ref = psi.copy()
+        for s in range(2):
+            E = h.step_graph(12, 0.25)
+            ref, E_ref = O.itp_step(ref, V, g, 12, 0.25)
+            err = float(np.max(np.abs(E - E_ref)) / np.max(np.abs(E_ref)))
+            report(f"128^3 {prec} graph step {s} {chosen}", err, ENERGY_TOL[prec])
+            assert err < ENERGY_TOL[prec]
+
+
+def test_batch_of_specialised_sizes_matches_oracle():
+    """A batch with one problem per specialised cubic edge (48, 64, 96) in
+    FP64: one batch step against the oracle's step of each problem."""
+    dims, boxes, ns, problems = [], [], [], []
+    for edge, n in ((48, 3), (64, 2), (96, 2)):
+        g = cubic(edge, 20.0)
+        V = wells_problem(g, seed=edge)
+        psi = seeded_states(g, n, seed=edge)
+        problems.append((g, V, psi))
+        dims.append((edge,) * 3)
+        boxes.append((20.0,) * 3)
+        ns.append(n)
+    with P.ItpBatch(dims, boxes, ns, precision=P.ITP_FP64) as b:
+        for q, (g, V, psi) in zip(b.problems, problems):
+            q.set_potential(V)
+            q.set_states(psi)
+        Eb = b.step(8, 0.25)
+    for p, (g, V, psi) in enumerate(problems):
+        _, E_ref = O.itp_step(psi, V, g, 8, 0.25)
+        err = float(np.max(np.abs(Eb[p] - E_ref)) / np.max(np.abs(E_ref)))
+        report(f"batch problem {p} ({g.nx}^3) fp64", err, 1e-11)
+        assert err < 1e-11
