@@ -121,6 +121,13 @@ def ncu_traffic(workload, kind):
     return rec["bytes"]
 
 
+def _hbm_peak():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except Exception:
+        return 6800.0
+
+
 def algorithmic_bytes(kind, g, m, s, mixed=False):
     """Bytes a launch of `kind` must move over m states (s = bytes per real):
     every pass reads and writes the half spectrum once; the potential factor
@@ -139,6 +146,31 @@ def algorithmic_bytes(kind, g, m, s, mixed=False):
         "plane_hpsi": (spec + 2 * m * N * s + N * s) if mixed
                       else (spec + m * N * s + N * 8 + m * N * 8),
     }.get(kind)
+
+
+def step_bytes(g, m, k, s=4):
+    """Algorithmic bytes of one whole mixed-path step (order 2k, Ritz values)
+    over m states on grid g with whole-plane passes: per term i a forward
+    plane pass, i pencils, i - 1 merged plane passes and the term pass; the
+    exact sum of the k FP32 term contributions into phi (k reads, one write);
+    the overlap Gram (phi once) and the update psi = L^-1 phi (read phi,
+    write psi); the energies (forward pass, kinetic pencil, H psi pass, the
+    subspace Gram reading psi and H psi).  The n x n work moves no
+    appreciable bytes."""
+    N = g.n_points
+    b = 0
+    for i in range(1, k + 1):
+        b += algorithmic_bytes("plane_fwd", g, m, s, mixed=True)
+        b += i * algorithmic_bytes("pencil", g, m, s, mixed=True)
+        b += (i - 1) * algorithmic_bytes("plane_merged", g, m, s, mixed=True)
+        b += algorithmic_bytes("plane_combine", g, m, s, mixed=True)
+    b += (k + 1) * m * N * 4                    # term sum
+    b += m * N * 4 + 2 * m * N * 4              # overlap Gram, update
+    b += (m * N * s + m * g.nz * g.ny * (g.nx // 2 + 1) * 2 * s   # forward (no factor)
+          + algorithmic_bytes("pencil_kinetic", g, m, s, mixed=True)
+          + algorithmic_bytes("plane_hpsi", g, m, s, mixed=True)
+          + 2 * m * N * 4)                      # subspace Gram
+    return b
 
 
 class ClockSampler:
@@ -722,6 +754,10 @@ def batch_throughput(P, torch, steps, warmup, count=64, order=8, tau=0.25, seed=
     sizes = {}
     for g, _, _ in probs:
         sizes[f"{g.nx}^3"] = sizes.get(f"{g.nx}^3", 0) + 1
+    # whole-step roofline of the batch: every problem's algorithmic bytes
+    # per step over the measured step time
+    hbm_peak = _hbm_peak()
+    step_b = sum(step_bytes(g, n, order // 2) for g, _, n in probs)
     return {"workload": f"{count} independent random-well problems (seed {seed}+p), grids "
                         f"{sizes}, n = 8..64 states each ({m_total} in all), order 8, "
                         f"tau = {tau}, mixed precision",
@@ -729,6 +765,12 @@ def batch_throughput(P, torch, steps, warmup, count=64, order=8, tau=0.25, seed=
             "ms_per_step": 1e3 * dt / steps, "steps": steps,
             "state_points": int(sum(n * g.n_points for g, _, n in probs)),
             "gpu_launches_per_step": per_step, "graph_launches_per_step": 1,
+            "roofline": {"bound": "hbm", "algorithmic_bytes_per_step": step_b,
+                         "achieved": step_b / (dt / steps) / 1e9, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": step_b / (dt / steps) / 1e9 / hbm_peak,
+                         "how": "sum over the problems of the whole step's algorithmic "
+                                "bytes (FFT passes, term sum, overlap, update, energies) "
+                                "over the measured time of one batch step"},
             "one_by_one": {"value": m_total * steps / dt_serial,
                            "ms_per_step": 1e3 * dt_serial / steps,
                            "how": "each problem's own itp_step graph, problems in turn "
@@ -941,6 +983,12 @@ def main():
             roof_all[k] = {"avg_launch_ms": round(t * 1e3, 4),
                            "achieved_gbs": round(b / t / 1e9, 1),
                            "frac": round(b / t / 1e9 / hbm_peak, 4)}
+    # the whole timed step against the same roofline: its algorithmic bytes
+    # (every pass, the term sum, overlap, update, energies) over the step time
+    sb = step_bytes(g, m, order // 2)
+    step_roof = {"bound": "hbm", "algorithmic_bytes_per_step": sb,
+                 "achieved": sb / (dt / args.steps) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                 "frac": sb / (dt / args.steps) / 1e9 / hbm_peak}
     total_prof = sum(v[1] for v in kinds.values())
     dt_prof = max_over_ranks(dt_prof)
     eager = {"value": replicas_value(m * args.steps, dt_prof, world), "unit": "state-steps/s",
@@ -1105,6 +1153,7 @@ def main():
             "launch_shapes": {"chosen": tuned, "autotune": tune_report},
             "roofline": roof,
             "rooflines_fft_passes": roof_all,
+            "step_roofline": step_roof,
             "kernel_breakdown": breakdown,
             "eager_profiled": eager,
             "fp64_path": fp64,

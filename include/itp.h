@@ -70,7 +70,9 @@ typedef struct itp_grid* itp_handle;
  *   nx, ny, nz   grid points per axis (see conventions)
  *   lx, ly, lz   box lengths (bohr), > 0
  *   n_states     wanted states n >= 1; n_guard >= 0 extra guard states;
- *                m = n + n_guard <= 128
+ *                m = n + n_guard <= 256 (the n x n work runs in blocks of
+ *                128 states: m > 128 costs up to four times the m <= 128
+ *                overlap and three times the update per block of states)
  *   precision    ITP_FP64 or ITP_MIXED
  *   cuda_stream  cudaStream_t to issue work on (NULL: default stream)
  * Allocates all device memory for the states, the half-spectrum workspace

@@ -14,26 +14,40 @@ namespace itp {
 
 namespace {
 
-constexpr int kMaxM = 128;
+constexpr int kMaxM = 256;   // states of the n x n work at most
+constexpr int kBlk = 128;    // rows of one state block of the Gram and apply kernels
 
 // ---------------------------------------------------------------------------
-// Gram partial sums over chunks of points.  512 threads as 16 (tx) x 32 (ty);
-// thread owns rows i = ty + 32*q (q < 4) and cols j = tx + 16*r (r < 8).
+// Gram partial sums over chunks of points.  The m x m result is cut into
+// 128 x 128 blocks; CTA (chunk c, block b) sums rows [128 bi, +128) of A
+// against rows [128 bj, +128) of B, (bi, bj) = block b of the list that
+// launch_gram_partial builds (with A == B only bj <= bi, each off-diagonal
+// block also written transposed).  512 threads as 16 (tx) x 32 (ty); thread
+// owns block rows i = ty + 32*q (q < 4) and cols j = tx + 16*r (r < 8).
 // points per shared tile: 32 (FP32) or 16 (FP64), 33 KB of shared tiles;
 // FP32 products are summed over runs of 256 points, then in FP64.
 template <typename TC> struct GramTile { static constexpr int KT = sizeof(TC) == 4 ? 32 : 16; };
 constexpr int kGramRun = 256;
 
+// Block b of the Gram kernels' block list: (bi, bj) packed as bi * 256 + bj.
+struct GramBlocks {
+  int n;
+  int ij[(kMaxM / kBlk) * (kMaxM / kBlk)];
+};
+
 template <typename TA, typename TB, typename TC>
 __global__ void __launch_bounds__(512) gram_partial_kernel(const TA* __restrict__ A,
                                                            const TB* __restrict__ B, int m,
                                                            long long N, long long chunk,
-                                                           double* __restrict__ partial) {
+                                                           double* __restrict__ partial,
+                                                           const GramBlocks blocks, int mirror) {
   constexpr int KT = GramTile<TC>::KT;
   constexpr int kFlushTiles = kGramRun / KT;
-  __shared__ TC sA[KT][kMaxM + 1];
-  __shared__ TC sB[KT][kMaxM + 1];
+  __shared__ TC sA[KT][kBlk + 1];
+  __shared__ TC sB[KT][kBlk + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int bi = blocks.ij[blockIdx.y] >> 8, bj = blocks.ij[blockIdx.y] & 255;
+  const int ia = kBlk * bi, jb = kBlk * bj;   // first row of A and of B
   const long long p_begin = (long long)blockIdx.x * chunk;
   const long long p_end = min(N, p_begin + chunk);
   double accd[4][8];
@@ -45,13 +59,13 @@ __global__ void __launch_bounds__(512) gram_partial_kernel(const TA* __restrict_
   int tiles_in_run = 0;
   for (long long p0 = p_begin; p0 < p_end; p0 += KT) {
     // load tiles: element (row i, point p0 + k)
-    for (int e = threadIdx.x; e < KT * kMaxM; e += blockDim.x) {
+    for (int e = threadIdx.x; e < KT * kBlk; e += blockDim.x) {
       const int i = e / KT, k = e - i * KT;
       const long long p = p0 + k;
       TC va = (TC)0, vb = (TC)0;
-      if (i < m && p < p_end) {
-        va = (TC)A[(long long)i * N + p];
-        vb = (TC)B[(long long)i * N + p];
+      if (p < p_end) {
+        if (ia + i < m) va = (TC)A[(long long)(ia + i) * N + p];
+        if (jb + i < m) vb = (TC)B[(long long)(jb + i) * N + p];
       }
       sA[k][i] = va;
       sB[k][i] = vb;
@@ -88,11 +102,15 @@ __global__ void __launch_bounds__(512) gram_partial_kernel(const TA* __restrict_
   double* out = partial + (long long)blockIdx.x * m * m;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const int i = ty + 32 * q;
+    const int i = ia + ty + 32 * q;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-      const int j = tx + 16 * r;
-      if (i < m && j < m) out[i * m + j] = accd[q][r] + (double)accf[q][r];
+      const int j = jb + tx + 16 * r;
+      if (i < m && j < m) {
+        const double v = accd[q][r] + (double)accf[q][r];
+        out[i * m + j] = v;
+        if (mirror && bi != bj) out[j * m + i] = v;
+      }
     }
   }
 }
@@ -123,35 +141,46 @@ __global__ void gram_reduce_kernel(const double* __restrict__ partial, int n_chu
 // Nothing a step reads remotely (column k of S, row k of R) is written in
 // that step, so one barrier per step orders everything.
 constexpr int kClus = 8;                      // CTAs per cluster (portable size)
-constexpr int kClusRows = kMaxM / kClus;      // rows per CTA at most
 constexpr int kClusThreads = 256;
-constexpr int kClusPitch = kMaxM + 1;
+
+// Shared memory of the cluster kernels: rp = ceil(m / kClus) rows of pitch
+// m + 1 (odd: conflict-free column reads), `mats` such matrices, plus
+// `vecs` vectors of m doubles.
+__host__ __device__ constexpr size_t clus_smem(int m, int mats, int vecs) {
+  return ((size_t)mats * ((m + kClus - 1) / kClus) * (m + 1) + (size_t)vecs * m) *
+         sizeof(double);
+}
 
 __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kClusThreads)
     cholesky_inverse_cluster_kernel(const double* __restrict__ S, int m,
                                     double* __restrict__ Minv, int* status) {
   cg::cluster_group cl = cg::this_cluster();
-  __shared__ double A[kClusRows][kClusPitch];
-  __shared__ double Rr[kClusRows][kClusPitch];
-  __shared__ double lf[kMaxM], mk[kMaxM];
+  extern __shared__ double csh[];
   __shared__ double s_piv;
   __shared__ int s_bad;
   const int rank = (int)cl.block_rank();
   const int rp = (m + kClus - 1) / kClus;
+  const int pitch = m + 1;
+  double* A_ = csh;                       // [rp][pitch] own rows of S (lower part)
+  double* Rr_ = A_ + (size_t)rp * pitch;  // [rp][pitch] own rows of R
+  double* lf = Rr_ + (size_t)rp * pitch;  // [m]
+  double* mk = lf + m;                    // [m]
+  auto A = [&](int il, int j) -> double& { return A_[il * pitch + j]; };
+  auto Rr = [&](int il, int j) -> double& { return Rr_[il * pitch + j]; };
   const int r0 = rank * rp, r1 = max(r0, min(m, r0 + rp));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = kClusThreads / 32;
   if (tid == 0) s_bad = 0;
   for (int q = tid; q < (r1 - r0) * m; q += kClusThreads) {
     const int il = q / m, j = q - il * m;
-    A[il][j] = S[(long long)(r0 + il) * m + j];
-    Rr[il][j] = (r0 + il == j) ? 1.0 : 0.0;
+    A(il, j) = S[(long long)(r0 + il) * m + j];
+    Rr(il, j) = (r0 + il == j) ? 1.0 : 0.0;
   }
   cl.sync();
   for (int k = 0; k < m; ++k) {
     const int ok = k / rp;
     if (tid == 0) {
-      const double akk = *cl.map_shared_rank(&A[k - ok * rp][k], ok);
+      const double akk = *cl.map_shared_rank(&A(k - ok * rp, k), ok);
       double piv = 1.0;
       if (!(akk > 0.0) || !isfinite(akk)) s_bad = 1;
       else piv = sqrt(akk);
@@ -161,10 +190,10 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kClusThreads)
     const double rpiv = 1.0 / s_piv;
     for (int j = k + 1 + tid; j < m; j += kClusThreads) {
       const int o = j / rp;
-      lf[j] = *cl.map_shared_rank(&A[j - o * rp][k], o) * rpiv;
+      lf[j] = *cl.map_shared_rank(&A(j - o * rp, k), o) * rpiv;
     }
     for (int j = tid; j <= k; j += kClusThreads)
-      mk[j] = *cl.map_shared_rank(&Rr[k - ok * rp][j], ok) * rpiv;
+      mk[j] = *cl.map_shared_rank(&Rr(k - ok * rp, j), ok) * rpiv;
     __syncthreads();
     if (rank == ok)
       for (int j = tid; j < m; j += kClusThreads) Minv[(long long)k * m + j] = j <= k ? mk[j] : 0.0;
@@ -173,8 +202,8 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kClusThreads)
       const int il = i - r0;
       const double li = lf[i];
       for (int j = lane; j <= i; j += 32) {
-        if (j <= k) Rr[il][j] -= li * mk[j];
-        else A[il][j] -= li * lf[j];
+        if (j <= k) Rr(il, j) -= li * mk[j];
+        else A(il, j) -= li * lf[j];
       }
     }
     cl.sync();
@@ -192,36 +221,40 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kClusThreads)
     tridiag_cluster_kernel(const double* __restrict__ H, int m, double* __restrict__ d,
                            double* __restrict__ e) {
   cg::cluster_group cl = cg::this_cluster();
-  __shared__ double A[kClusRows][kClusPitch];
-  __shared__ double vf[kMaxM], wf[kMaxM];
-  __shared__ double pl[kClusRows];       // own entries of p (read by the others)
+  extern __shared__ double csh[];
   __shared__ double s_sig[2], s_dot[2];  // partial sums (read by the others)
   __shared__ double s_beta, s_K;
   const int rank = (int)cl.block_rank();
   const int rp = (m + kClus - 1) / kClus;
+  const int pitch = m + 1;
+  double* A_ = csh;                       // [rp][pitch] own rows
+  double* vf = A_ + (size_t)rp * pitch;   // [m]
+  double* wf = vf + m;                    // [m]
+  double* pl = wf + m;                    // [m] (rp used): own entries of p (read by the others)
+  auto A = [&](int il, int j) -> double& { return A_[il * pitch + j]; };
   const int r0 = rank * rp, r1 = max(r0, min(m, r0 + rp));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = kClusThreads / 32;
   for (int q = tid; q < (r1 - r0) * m; q += kClusThreads) {
     const int il = q / m, j = q - il * m, i = r0 + il;
-    A[il][j] = 0.5 * (H[(long long)i * m + j] + H[(long long)j * m + i]);
+    A(il, j) = 0.5 * (H[(long long)i * m + j] + H[(long long)j * m + i]);
   }
   __syncthreads();
   for (int k = 0; k + 2 < m; ++k) {
     const int n0 = k + 1, b = k & 1;
     if (warp == 0) {
       double sig = 0.0;
-      for (int i = max(r0, n0 + 1) + lane; i < r1; i += 32) sig += A[i - r0][k] * A[i - r0][k];
+      for (int i = max(r0, n0 + 1) + lane; i < r1; i += 32) sig += A(i - r0, k) * A(i - r0, k);
       for (int o = 16; o; o >>= 1) sig += __shfl_xor_sync(0xffffffffu, sig, o);
       if (lane == 0) s_sig[b] = sig;
     }
-    if (tid == 0 && k >= r0 && k < r1) d[k] = A[k - r0][k];
+    if (tid == 0 && k >= r0 && k < r1) d[k] = A(k - r0, k);
     cl.sync();
     if (tid == 0) {
       double sig = 0.0;
       for (int r = 0; r < kClus; ++r) sig += *cl.map_shared_rank(&s_sig[b], r);
       const int o = n0 / rp;
-      const double x0 = *cl.map_shared_rank(&A[n0 - o * rp][k], o);
+      const double x0 = *cl.map_shared_rank(&A(n0 - o * rp, k), o);
       double alpha = x0, beta = 0.0, v0 = 0.0;
       if (sig != 0.0) {
         const double nrm = sqrt(x0 * x0 + sig);
@@ -235,13 +268,13 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kClusThreads)
     }
     for (int j = n0 + 1 + tid; j < m; j += kClusThreads) {
       const int o = j / rp;
-      vf[j] = *cl.map_shared_rank(&A[j - o * rp][k], o);
+      vf[j] = *cl.map_shared_rank(&A(j - o * rp, k), o);
     }
     __syncthreads();
     const double beta = s_beta;
     for (int i = max(r0, n0) + warp; i < r1; i += NW) {
       double acc = 0.0;
-      for (int j = n0 + lane; j < m; j += 32) acc += A[i - r0][j] * vf[j];
+      for (int j = n0 + lane; j < m; j += 32) acc += A(i - r0, j) * vf[j];
       for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
       if (lane == 0) pl[i - r0] = beta * acc;
     }
@@ -268,14 +301,14 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kClusThreads)
     for (int i = max(r0, n0) + warp; i < r1; i += NW) {
       const int il = i - r0;
       const double vi = vf[i], wi = wf[i];
-      for (int j = n0 + lane; j < m; j += 32) A[il][j] -= vi * wf[j] + wi * vf[j];
+      for (int j = n0 + lane; j < m; j += 32) A(il, j) -= vi * wf[j] + wi * vf[j];
     }
     __syncthreads();
   }
   if (tid == 0) {
-    if (m >= 2 && m - 2 >= r0 && m - 2 < r1) d[m - 2] = A[m - 2 - r0][m - 2];
-    if (m >= 2 && m - 1 >= r0 && m - 1 < r1) e[m - 2] = A[m - 1 - r0][m - 2];
-    if (m - 1 >= r0 && m - 1 < r1) d[m - 1] = A[m - 1 - r0][m - 1];
+    if (m >= 2 && m - 2 >= r0 && m - 2 < r1) d[m - 2] = A(m - 2 - r0, m - 2);
+    if (m >= 2 && m - 1 >= r0 && m - 1 < r1) e[m - 2] = A(m - 1 - r0, m - 2);
+    if (m - 1 >= r0 && m - 1 < r1) d[m - 1] = A(m - 1 - r0, m - 1);
   }
   cl.sync();   // no CTA leaves while another may still read its shared memory
 }
@@ -287,12 +320,15 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kClusThreads)
 __global__ void __launch_bounds__(1024) jacobi_kernel(const double* __restrict__ H, int m,
                                                       double* __restrict__ E,
                                                       double* __restrict__ Rt,
-                                                      double* __restrict__ Ut, int* status) {
+                                                      double* __restrict__ Ut,
+                                                      double* __restrict__ Aglob, int* status) {
   extern __shared__ double sh[];
   const int mm = (m + 1) & ~1;          // even number of players (a dummy if m is odd)
   const int P = m + 1;
-  double* A = sh;                        // m x P
-  double* cs = sh + m * P;               // [mm/2] c, [mm/2] s
+  // m x P working matrix: in shared memory, or (Aglob set: too large for
+  // one CTA) in global memory, where it stays in L2
+  double* A = Aglob ? Aglob : sh;
+  double* cs = Aglob ? sh : sh + m * P;  // [mm/2] c, [mm/2] s
   int* pr = reinterpret_cast<int*>(cs + mm);   // [mm/2] p, [mm/2] q
   __shared__ double off_norm, tot_norm;
   __shared__ int done;
@@ -522,48 +558,60 @@ __global__ void residual_final_kernel(const double* __restrict__ partial, int ch
 }
 
 // ---------------------------------------------------------------------------
-// Y = M X.  Persistent CTAs over tiles of 32 points; M (as TC) stays in
-// shared memory.  512 threads: tx = point in tile, ty = row group (16 rows).
+// Y[r0 + i] (=|+=) sum_k M[r0 + i][k0 + k] X[k0 + k] for i < nr, k < nk: one
+// block of Y = M X (the host walks the blocks of 128 rows).  Persistent CTAs
+// over tiles of 32 points; the M block (as TC) stays in shared memory.  512
+// threads: tx = point in tile, ty = row group (16 rows).  lower: M[i][k] = 0
+// for k > i (global indices).  add: the block's product is added to Y.
 constexpr int kApplyPT = 32;
 
 template <typename TX, typename TY, typename TC>
 __global__ void __launch_bounds__(512) apply_matrix_kernel(const double* __restrict__ M, int m,
                                                            int lower, const TX* __restrict__ X,
-                                                           TY* __restrict__ Y, long long N) {
+                                                           TY* __restrict__ Y, long long N,
+                                                           int r0, int nr, int k0, int nk,
+                                                           int add) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  TC* sM = reinterpret_cast<TC*>(smraw);            // m x m
-  TC* sX = sM + m * m;                              // m x kApplyPT
+  TC* sM = reinterpret_cast<TC*>(smraw);            // nr x nk
+  TC* sX = sM + nr * nk;                            // nk x kApplyPT
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // ty in 0..15
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) sM[e] = (TC)M[e];
+  for (int e = threadIdx.x; e < nr * nk; e += blockDim.x) {
+    const int i = e / nk, k = e - i * nk;
+    sM[e] = (TC)M[(long long)(r0 + i) * m + k0 + k];
+  }
   const long long ntiles = (N + kApplyPT - 1) / kApplyPT;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long p0 = tile * kApplyPT;
     __syncthreads();
-    for (int e = threadIdx.x; e < m * kApplyPT; e += blockDim.x) {
+    for (int e = threadIdx.x; e < nk * kApplyPT; e += blockDim.x) {
       const int k = e / kApplyPT, j = e - k * kApplyPT;
       const long long p = p0 + j;
-      sX[e] = (p < N) ? (TC)X[(long long)k * N + p] : (TC)0;
+      sX[e] = (p < N) ? (TC)X[(long long)(k0 + k) * N + p] : (TC)0;
     }
     __syncthreads();
     const long long p = p0 + tx;
-    for (int i0 = ty; i0 < m; i0 += 16 * 8) {
+    for (int i0 = ty; i0 < nr; i0 += 16 * 8) {
       TC acc[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) acc[q] = (TC)0;
-      const int kmax = lower ? min(m, i0 + 16 * 7 + 1) : m;
+      // lower triangular: row r0 + i needs k0 + k <= r0 + i
+      const int kmax = lower ? max(0, min(nk, r0 + i0 + 16 * 7 + 1 - k0)) : nk;
       for (int k = 0; k < kmax; ++k) {
         const TC x = sX[k * kApplyPT + tx];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int i = i0 + 16 * q;
-          if (i < m) acc[q] = fma(sM[i * m + k], x, acc[q]);
+          if (i < nr) acc[q] = fma(sM[i * nk + k], x, acc[q]);
         }
       }
       if (p < N) {
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int i = i0 + 16 * q;
-          if (i < m) Y[(long long)i * N + p] = (TY)acc[q];
+          if (i < nr) {
+            TY* y = Y + (long long)(r0 + i) * N + p;
+            *y = add ? (TY)((TC)*y + acc[q]) : (TY)acc[q];
+          }
         }
       }
     }
@@ -586,10 +634,18 @@ template <> struct ComputeOf<double> { using type = double; };
 template <typename TA, typename TB, typename TC>
 cudaError_t launch_gram_partial(const TA* A, const TB* B, int m, long long n_points, int n_chunks,
                                 double* partial, cudaStream_t st) {
-  if (m > kMaxM) return cudaErrorInvalidValue;
+  if (m < 1 || m > kMaxM) return cudaErrorInvalidValue;
   long long chunk = (n_points + n_chunks - 1) / n_chunks;
   chunk = (chunk + kGramRun - 1) / kGramRun * kGramRun;
-  gram_partial_kernel<TA, TB, TC><<<n_chunks, 512, 0, st>>>(A, B, m, n_points, chunk, partial);
+  // 128 x 128 blocks of the result; A A^T: the lower blocks, mirrored
+  const bool same = (const void*)A == (const void*)B;
+  const int nb = (m + kBlk - 1) / kBlk;
+  GramBlocks blocks{};
+  for (int bi = 0; bi < nb; ++bi)
+    for (int bj = 0; bj < nb; ++bj)
+      if (!same || bj <= bi) blocks.ij[blocks.n++] = bi * 256 + bj;
+  gram_partial_kernel<TA, TB, TC><<<dim3(n_chunks, blocks.n), 512, 0, st>>>(
+      A, B, m, n_points, chunk, partial, blocks, same ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -602,26 +658,39 @@ cudaError_t launch_gram_reduce(const double* partial, int n_chunks, int m, doubl
 cudaError_t launch_cholesky_inverse(const double* S, int m, double* Minv, int* status,
                                     cudaStream_t st) {
   if (m < 1 || m > kMaxM) return cudaErrorInvalidValue;
-  cholesky_inverse_cluster_kernel<<<kClus, kClusThreads, 0, st>>>(S, m, Minv, status);
+  const size_t smem = clus_smem(m, 2, 2);
+  cudaError_t e = cudaFuncSetAttribute(cholesky_inverse_cluster_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cholesky_inverse_cluster_kernel<<<kClus, kClusThreads, smem, st>>>(S, m, Minv, status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_jacobi_eigh(const double* H, int m, double* E, double* Rt, double* work,
                                int* status, cudaStream_t st) {
-  if (m > kMaxM) return cudaErrorInvalidValue;
+  if (m < 1 || m > kMaxM) return cudaErrorInvalidValue;
   const int mm = (m + 1) & ~1;
-  const size_t smem = (size_t)m * (m + 1) * sizeof(double) + (size_t)mm * sizeof(double) +
-                      (size_t)mm * sizeof(int);
+  const size_t amat = (size_t)m * (m + 1) * sizeof(double);
+  const size_t rest = (size_t)mm * sizeof(double) + (size_t)mm * sizeof(int);
+  // the working matrix goes to global memory (after U^T in work) when it
+  // does not fit one CTA's shared memory
+  const bool global_a = amat + rest > 227 * 1024;
+  const size_t smem = global_a ? rest : amat + rest;
   cudaError_t e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  jacobi_kernel<<<1, 1024, smem, st>>>(H, m, E, Rt, work, status);
+  jacobi_kernel<<<1, 1024, smem, st>>>(H, m, E, Rt, work,
+                                       global_a ? work + (size_t)m * m : nullptr, status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tridiag(const double* H, int m, double* work, cudaStream_t st) {
   if (m < 1 || m > kMaxM) return cudaErrorInvalidValue;
-  tridiag_cluster_kernel<<<kClus, kClusThreads, 0, st>>>(H, m, work, work + m);
+  const size_t smem = clus_smem(m, 1, 3);
+  cudaError_t e = cudaFuncSetAttribute(tridiag_cluster_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  tridiag_cluster_kernel<<<kClus, kClusThreads, smem, st>>>(H, m, work, work + m);
   return cudaGetLastError();
 }
 
@@ -668,7 +737,7 @@ template cudaError_t launch_axpby<double>(double, const double*, double, const d
                                           double*, long long, cudaStream_t);
 
 cudaError_t launch_diag(const double* H, int m, double* E, cudaStream_t st) {
-  diag_kernel<<<1, 128, 0, st>>>(H, m, E);
+  diag_kernel<<<(m + 127) / 128, 128, 0, st>>>(H, m, E);
   return cudaGetLastError();
 }
 
@@ -676,8 +745,9 @@ template <typename TX, typename TY>
 cudaError_t launch_apply_matrix(const double* M, int m, int lower, const TX* X, TY* Y,
                                 long long n_points, cudaStream_t st) {
   using TC = typename ComputeOf<TY>::type;
-  if (m > kMaxM) return cudaErrorInvalidValue;
-  const size_t smem = ((size_t)m * m + (size_t)m * kApplyPT) * sizeof(TC);
+  if (m < 1 || m > kMaxM) return cudaErrorInvalidValue;
+  const int bm = m < kBlk ? m : kBlk;   // rows of an M block
+  const size_t smem = ((size_t)bm * bm + (size_t)bm * kApplyPT) * sizeof(TC);
   cudaError_t e = cudaFuncSetAttribute(apply_matrix_kernel<TX, TY, TC>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -687,8 +757,19 @@ cudaError_t launch_apply_matrix(const double* M, int m, int lower, const TX* X, 
   const long long ntiles = (n_points + kApplyPT - 1) / kApplyPT;
   const long long cap = (long long)sms * (smem > 110000 ? 1 : 2);
   const int blocks = (int)(ntiles < cap ? ntiles : cap);
-  apply_matrix_kernel<TX, TY, TC><<<blocks, 512, smem, st>>>(M, m, lower, X, Y, n_points);
-  return cudaGetLastError();
+  // Y block bi = sum over bk of M[bi][bk] X[bk] (bk <= bi when lower), in
+  // stream order: the first block product sets Y[bi], the others add to it
+  for (int r0 = 0; r0 < m; r0 += kBlk) {
+    const int nr = m - r0 < kBlk ? m - r0 : kBlk;
+    for (int k0 = 0; k0 < m && (!lower || k0 <= r0 + nr - 1); k0 += kBlk) {
+      const int nk = m - k0 < kBlk ? m - k0 : kBlk;
+      apply_matrix_kernel<TX, TY, TC><<<blocks, 512, smem, st>>>(M, m, lower, X, Y, n_points,
+                                                                 r0, nr, k0, nk, k0 > 0);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
 }
 
 template <typename TS, typename TD>
@@ -700,15 +781,6 @@ cudaError_t launch_convert(const TS* src, TD* dst, long long count, cudaStream_t
 template cudaError_t launch_gram_partial<double, double, double>(const double*, const double*, int,
                                                                  long long, int, double*,
                                                                  cudaStream_t);
-template cudaError_t launch_gram_partial<double, double, float>(const double*, const double*, int,
-                                                                long long, int, double*,
-                                                                cudaStream_t);
-template cudaError_t launch_gram_partial<float, double, float>(const float*, const double*, int,
-                                                               long long, int, double*,
-                                                               cudaStream_t);
-template cudaError_t launch_gram_partial<float, double, double>(const float*, const double*, int,
-                                                                long long, int, double*,
-                                                                cudaStream_t);
 template cudaError_t launch_apply_matrix<double, double>(const double*, int, int, const double*,
                                                          double*, long long, cudaStream_t);
 template cudaError_t launch_apply_matrix<double, float>(const double*, int, int, const double*,

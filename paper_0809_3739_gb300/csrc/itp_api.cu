@@ -19,7 +19,7 @@ using namespace itp;
 
 namespace {
 
-constexpr int kMaxStates = 128;
+constexpr int kMaxStates = 256;   // two 128-state blocks of the n x n work
 constexpr int kMaxTerms = 6;   // order <= 12
 constexpr int kHostChunks = 4; // state chunks of the host-buffer step (copy/compute overlap)
 constexpr size_t kSmemLimit = 227 * 1024;
@@ -155,6 +155,15 @@ void prof_end(itp_handle h, long idx) {
     int r_ = (expr);              \
     if (r_ != ITP_OK) return r_;  \
   } while (0)
+
+// Kernels behind one launch_* call of the n x n work, which walks 128-state
+// blocks when m > 128: the update Y = M X (lower: M lower triangular) and
+// the tensor-core Gram (A A^T: diagonal and off-diagonal blocks apart).
+int apply_launches(int m, bool lower) {
+  const int nb = (m + 127) / 128;
+  return lower ? nb * (nb + 1) / 2 : nb * nb;
+}
+int tc_gram_launches(int m, bool same) { return same && m > 128 ? 2 : 1; }
 
 // Wait limit for the next tensor-core launch: 0 (the kernels' own launch
 // deadline), or the short limit of the failure-detection test hook
@@ -436,6 +445,7 @@ int orthonormalize_lane<double>(itp_handle h) {
   ITP_LAUNCH(h, ITP_KERNEL_CHOLESKY, launch_cholesky_inverse(h->S, h->m, h->Mx, h->status, h->st));
   ITP_LAUNCH(h, ITP_KERNEL_APPLY, (launch_apply_matrix<double, double>(
                                       h->Mx, h->m, 1, h->acc, L.psi, h->g.n_points, h->st)));
+  h->launches += apply_launches(h->m, true) - 1;
   return ITP_OK;
 }
 // Mixed path: phi is FP32 (rounded from the FP64 sum) in psi_tmp; S and the
@@ -447,12 +457,14 @@ int orthonormalize_lane<float>(itp_handle h) {
                                                                h->g.n_points, h->n_chunks_tc,
                                                                h->partial, h->status, h->st,
                                                                tc_expire(h))));
+  h->launches += tc_gram_launches(h->m, true) - 1;
   ITP_LAUNCH(h, ITP_KERNEL_GRAM_REDUCE,
              launch_gram_reduce(h->partial, h->n_chunks_tc, h->m, h->dV, 1, h->S, h->st));
   ITP_LAUNCH(h, ITP_KERNEL_CHOLESKY, launch_cholesky_inverse(h->S, h->m, h->Mx, h->status, h->st));
   ITP_LAUNCH(h, ITP_KERNEL_APPLY, (launch_tc_apply<float, float>(h->Mx, h->m, L.psi_tmp, L.psi,
                                                                  h->g.n_points, h->status,
-                                                                 h->st, tc_expire(h))));
+                                                                 h->st, tc_expire(h), 1)));
+  h->launches += apply_launches(h->m, true) - 1;
   return ITP_OK;
 }
 
@@ -521,11 +533,13 @@ int energies_lane(itp_handle h, int flags) {
                                           h->Mx, h->m, reinterpret_cast<const float*>(L.psi),
                                           reinterpret_cast<float*>(L.psi_tmp), g.n_points,
                                           h->status, h->st, tc_expire(h))));
+      h->launches += apply_launches(h->m, false) - 1;
     } else {
       ITP_LAUNCH(h, ITP_KERNEL_APPLY, (launch_apply_matrix<double, double>(
                                           h->Mx, h->m, 0, reinterpret_cast<const double*>(L.psi),
                                           reinterpret_cast<double*>(L.psi_tmp), g.n_points,
                                           h->st)));
+      h->launches += apply_launches(h->m, false) - 1;
     }
     R* t = L.psi;
     L.psi = L.psi_tmp;
@@ -1144,7 +1158,9 @@ int itp_create_grid(itp_handle* out, int nx, int ny, int nz, double lx, double l
   ITP_CREATE(cuda(cudaMalloc(&h->S, m * m * sizeof(double)), "S"));
   ITP_CREATE(cuda(cudaMalloc(&h->Mx, m * m * sizeof(double)), "M"));
   ITP_CREATE(cuda(cudaMalloc(&h->Hs, m * m * sizeof(double)), "H_sub"));
-  ITP_CREATE(cuda(cudaMalloc(&h->Wmm, m * m * sizeof(double)), "work"));
+  // eigen-decomposition work: U^T, and the Jacobi matrix when it does not
+  // fit one CTA's shared memory
+  ITP_CREATE(cuda(cudaMalloc(&h->Wmm, (2 * m + 1) * m * sizeof(double)), "work"));
   ITP_CREATE(cuda(cudaMalloc(&h->E_dev, m * sizeof(double)), "E"));
   ITP_CREATE(cuda(cudaMalloc(&h->status, sizeof(int)), "status"));
   ITP_CREATE(cuda(cudaMemset(h->status, 0, sizeof(int)), "status"));

@@ -170,7 +170,7 @@ cudaError_t launch_diag(const double* H, int m, double* E, cudaStream_t st);
 template <typename TX, typename TY>
 cudaError_t launch_apply_matrix(const double* M, int m, int lower, const TX* X, TY* Y,
                                 long long n_points, cudaStream_t st);
-// Tensor-core (tcgen05 TF32, 3xTF32 split) versions, m <= 128; status gets
+// Tensor-core (tcgen05 TF32, 3xTF32 split) versions, m <= 256; status gets
 // bit 4 if a bounded mbarrier wait expired (the kernel then leaves its
 // output unwritten).  expire_ns != 0 is the failure-detection test hook:
 // every CTA first waits, with that limit and before issuing any copy or
@@ -180,9 +180,12 @@ cudaError_t launch_apply_matrix(const double* M, int m, int lower, const TX* X, 
 cudaError_t launch_tc_gram(const float* A, const float* B, int m, long long n_points,
                            int n_chunks, double* partial, int* status, cudaStream_t st,
                            unsigned long long expire_ns = 0);
+// Apply: lower != 0 skips the blocks of M above the diagonal (zero for the
+// inverse Cholesky factor); with m > 128 the launch walks 128-row blocks.
 template <typename TX, typename TY>
 cudaError_t launch_tc_apply(const double* M, int m, const TX* X, TY* Y, long long n_points,
-                            int* status, cudaStream_t st, unsigned long long expire_ns = 0);
+                            int* status, cudaStream_t st, unsigned long long expire_ns = 0,
+                            int lower = 0);
 // Precision conversion of whole state blocks.
 template <typename TS, typename TD>
 cudaError_t launch_convert(const TS* src, TD* dst, long long count, cudaStream_t st);

@@ -3,7 +3,10 @@
 //           Eq. (4), subspace matrix of the Ritz step)
 //   apply:  Y = M X over all points                         (psi = L^{-1} phi
 //           of Eq. (4), rotation onto Ritz vectors)
-// with X, Y the state blocks [m][N] (m <= 128) and M an m x m FP64 matrix.
+// with X, Y the state blocks [m][N] (m <= 256) and M an m x m FP64 matrix.
+// One MMA tile covers 128 states; m > 128 is cut into 128-row blocks: the
+// Gram into blocks (bi, bj) of the result (one CTA column per block), the
+// update into block products Y[bi] (=|+=) M[bi][bk] X[bk], one launch each.
 //
 // Precision: every operand is split into TF32 hi + lo parts (round to
 // nearest) by the warps that stage it into shared memory, and each product
@@ -228,11 +231,20 @@ constexpr int kTileBytes = 128 * kGramKT * 4;        // 16 KB per operand part
 // canonical layout of one of two MMA stages; one thread issues the MMAs.
 constexpr int kRawBytes = 128 * kGramKT * 4;        // 16 KB per operand
 
+// Result blocks of one Gram launch: block b = blockIdx.y covers rows
+// [128 bi, +128) of A against rows [128 bj, +128) of B, (bi, bj) packed as
+// bi * 256 + bj; mirror: also write the block transposed.
+struct TcBlocks {
+  int n;
+  int ij[4];
+};
+
 template <bool SAME>
 __global__ void __launch_bounds__(kTcThreads, 1)
     tc_gram_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    int m, long long N, long long chunk, double* __restrict__ partial,
-                   int* status, unsigned long long expire_ns) {
+                   int* status, unsigned long long expire_ns, const TcBlocks blocks,
+                   int mirror) {
   constexpr int NOPS = SAME ? 1 : 2;                // operands per tile
   constexpr int RAW = SAME ? 4 : 3;                 // raw ring depth
   extern __shared__ __align__(1024) unsigned char smraw[];
@@ -286,11 +298,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const long long p_end = min(N, p_begin + chunk);
   const int ntiles = p_end > p_begin ? (int)((p_end - p_begin + kGramKT - 1) / kGramKT) : 0;
 
+  const int bi = blocks.ij[blockIdx.y] >> 8, bj = blocks.ij[blockIdx.y] & 255;
   auto issue = [&](int t, int r) {   // one thread
     const int x = (int)(p_begin + (long long)t * kGramKT);
     mbar_arrive_expect_tx(&full[r], (uint32_t)(NOPS * kRawBytes));
-    tma_load_2d(raw(r, 0), &tmA, x, 0, &full[r]);
-    if (!SAME) tma_load_2d(raw(r, 1), &tmB, x, 0, &full[r]);
+    tma_load_2d(raw(r, 0), &tmA, x, 128 * bi, &full[r]);
+    if (!SAME) tma_load_2d(raw(r, 1), &tmB, x, 128 * bj, &full[r]);
   };
   // tiles [0, issued) have their copies issued, [0, committed) their MMAs
   int issued = 0, committed = 0, t_stop = 0;
@@ -390,12 +403,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
   } else {
     double* out = partial + (long long)blockIdx.x * m * m;
-    const int i = quad * 32 + lane;
+    const int i = 128 * bi + quad * 32 + lane;
     if (i < m) {
 #pragma unroll
       for (int q = 0; q < 64; ++q) {
-        const int j = chalf * 64 + q;
-        if (j < m) out[(long long)i * m + j] = (double)acc[q];
+        const int j = 128 * bj + chalf * 64 + q;
+        if (j < m) {
+          out[(long long)i * m + j] = (double)acc[q];
+          if (mirror) out[(long long)j * m + i] = (double)acc[q];
+        }
       }
     }
   }
@@ -453,6 +469,7 @@ static_assert(kTcThreads == 256, "one (4 points, 4 states) group per thread");
 template <typename TX>
 __device__ __forceinline__ void load_points(const TX* __restrict__ X, int m, long long N,
                                             long long p0, float (&v)[4][4]) {
+  // X points at the block's first state row; m = its rows
   const int L = threadIdx.x;
   const int n4 = L & 7, k4 = L >> 3;   // k4 in 0..31
   const long long p = p0 + 4 * n4;
@@ -496,7 +513,7 @@ __device__ __forceinline__ void store_points(const float (&v)[4][4], uint32_t hi
 template <typename TY>
 __device__ __forceinline__ bool apply_epilogue(uint32_t tmem_col, float* stage, int m,
                                                TY* __restrict__ Y, long long N, long long p0,
-                                               bool ok) {
+                                               bool ok, int add) {
   constexpr int NT = 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // TMEM loads are warp-collective: a warp loads only if all its lanes saw the MMAs end
@@ -517,23 +534,31 @@ __device__ __forceinline__ bool apply_epilogue(uint32_t tmem_col, float* stage, 
     const int i = L >> 3, c4 = L & 7;
     if (i >= m) continue;
     const long long p = p0 + 4 * c4;
-    const float4 v = *reinterpret_cast<const float4*>(stage + i * (NT + 4) + 4 * c4);
+    float4 v = *reinterpret_cast<const float4*>(stage + i * (NT + 4) + 4 * c4);
     TY* dst = Y + (long long)i * N + p;
     if (p + 3 < N) {
+      if (add) {
+        const float4 o = *reinterpret_cast<const float4*>(dst);
+        v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
+      }
       *reinterpret_cast<float4*>(dst) = v;
     } else {
       const float w[4] = {v.x, v.y, v.z, v.w};
       for (int q = 0; q < 4; ++q)
-        if (p + q < N) dst[q] = w[q];
+        if (p + q < N) dst[q] = add ? dst[q] + w[q] : w[q];
     }
   }
   return true;
 }
 
+// One block product Y[r0 + i] (=|+=) sum_k M[r0 + i][k0 + k] X[k0 + k],
+// i < nr, k < nk (both <= 128): Mg is the full m x m matrix (row pitch m),
+// X and Y already point at rows k0 and r0; add: the product is added to Y.
 template <typename TX, typename TY>
 __global__ void __launch_bounds__(kTcThreads, 1)
-    tc_apply_kernel(const double* __restrict__ Mg, int m, const TX* __restrict__ X,
-                    TY* __restrict__ Y, long long N, int* status, unsigned long long expire_ns) {
+    tc_apply_kernel(const double* __restrict__ Mg, int m, int r0, int nr, int k0, int nk,
+                    int add, const TX* __restrict__ X, TY* __restrict__ Y, long long N,
+                    int* status, unsigned long long expire_ns) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ uint32_t tmem_base;
@@ -557,11 +582,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int i = (L >> 8) * 8 + (L & 7);
     const int k4 = (L >> 3) & 31;
     float v[4] = {0.f, 0.f, 0.f, 0.f};
-    if (i < m) {
+    if (i < nr) {
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int k = 4 * k4 + e;
-        if (k < m) v[e] = (float)Mg[i * m + k];
+        if (k < nk) v[e] = (float)Mg[(long long)(r0 + i) * m + k0 + k];
       }
     }
     // M = hi + lo, both TF32 parts of the FP32-rounded matrix
@@ -591,7 +616,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   bool aborted = __syncthreads_or(!ok) != 0;
   float cur[4][4], nxt[4][4];
   if ((long long)blockIdx.x < ntiles && !aborted)
-    load_points(X, m, N, (long long)blockIdx.x * kApplyNT, cur);
+    load_points(X, nk, N, (long long)blockIdx.x * kApplyNT, cur);
   for (long long tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x, ++local) {
     const int s = local & 1;
     ok = true;
@@ -601,7 +626,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     store_points(cur, xpart(s, 0), xpart(s, 1));
     const long long next = tile + gridDim.x;
-    if (next < ntiles) load_points(X, m, N, next * kApplyNT, nxt);   // in flight meanwhile
+    if (next < ntiles) load_points(X, nk, N, next * kApplyNT, nxt);   // in flight meanwhile
     fence_async_smem();
     tc_fence_before();
     if (__syncthreads_or(!ok)) {   // a wait expired somewhere in the CTA
@@ -632,8 +657,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int ps = (local - 1) & 1;
       ok = mbar_wait(&bar[ps], (uint32_t)(((local - 1) >> 1) & 1), deadline);
       tc_fence_after();
-      if (!apply_epilogue(tmem + (uint32_t)(ps * kApplyNT), ostage, m, Y, N,
-                          prev_tile * kApplyNT, ok)) {
+      if (!apply_epilogue(tmem + (uint32_t)(ps * kApplyNT), ostage, nr, Y, N,
+                          prev_tile * kApplyNT, ok, add)) {
         aborted = true;
         break;
       }
@@ -649,8 +674,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int ps = (local - 1) & 1;
     ok = mbar_wait(&bar[ps], (uint32_t)(((local - 1) >> 1) & 1), deadline);
     tc_fence_after();
-    if (apply_epilogue(tmem + (uint32_t)(ps * kApplyNT), ostage, m, Y, N, prev_tile * kApplyNT,
-                       ok))
+    if (apply_epilogue(tmem + (uint32_t)(ps * kApplyNT), ostage, nr, Y, N, prev_tile * kApplyNT,
+                       ok, add))
       pending &= ~(1u << ps);
     else
       aborted = true;
@@ -674,7 +699,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 cudaError_t launch_tc_gram(const float* A, const float* B, int m, long long n_points,
                            int n_chunks, double* partial, int* status, cudaStream_t st,
                            unsigned long long expire_ns) {
-  if (m > 128 || m < 1 || (n_points % 8) || n_points >= (1LL << 31)) return cudaErrorInvalidValue;
+  if (m > 256 || m < 1 || (n_points % 8) || n_points >= (1LL << 31)) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15)
     return cudaErrorInvalidValue;
   long long chunk = (n_points + n_chunks - 1) / n_chunks;
@@ -683,29 +708,43 @@ cudaError_t launch_tc_gram(const float* A, const float* B, int m, long long n_po
   CUtensorMap tmA, tmB;
   if (!make_rows_map(&tmA, A, m, n_points) || !make_rows_map(&tmB, B, m, n_points))
     return cudaErrorNotSupported;
-  const int nops = same ? 1 : 2, raw = same ? 4 : 3;
-  const size_t smem = (size_t)2 * nops * 2 * kTileBytes + (size_t)raw * nops * kRawBytes + 1024;
+  // 128 x 128 result blocks: A A^T takes the diagonal blocks with one operand
+  // per tile and the lower off-diagonal ones (mirrored) with two; A B^T
+  // takes every block with two operands
+  const int nb = (m + 127) / 128;
+  TcBlocks diag{}, pair{};
+  for (int bi = 0; bi < nb; ++bi)
+    for (int bj = 0; bj < nb; ++bj) {
+      if (same && bi == bj) diag.ij[diag.n++] = bi * 256 + bj;
+      else if (!same || bj < bi) pair.ij[pair.n++] = bi * 256 + bj;
+    }
   cudaError_t e;
-  if (same) {
+  if (diag.n) {
+    const size_t smem = (size_t)2 * 1 * 2 * kTileBytes + (size_t)4 * 1 * kRawBytes + 1024;
     e = cudaFuncSetAttribute(tc_gram_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
-    tc_gram_kernel<true><<<n_chunks, kTcThreads, smem, st>>>(tmA, tmB, m, n_points, chunk,
-                                                             partial, status, expire_ns);
-  } else {
+    tc_gram_kernel<true><<<dim3(n_chunks, diag.n), kTcThreads, smem, st>>>(
+        tmA, tmB, m, n_points, chunk, partial, status, expire_ns, diag, 0);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (pair.n) {
+    const size_t smem = (size_t)2 * 2 * 2 * kTileBytes + (size_t)3 * 2 * kRawBytes + 1024;
     e = cudaFuncSetAttribute(tc_gram_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
-    tc_gram_kernel<false><<<n_chunks, kTcThreads, smem, st>>>(tmA, tmB, m, n_points, chunk,
-                                                              partial, status, expire_ns);
+    tc_gram_kernel<false><<<dim3(n_chunks, pair.n), kTcThreads, smem, st>>>(
+        tmA, tmB, m, n_points, chunk, partial, status, expire_ns, pair, same ? 1 : 0);
   }
   return cudaGetLastError();
 }
 
 template <typename TX, typename TY>
 cudaError_t launch_tc_apply(const double* M, int m, const TX* X, TY* Y, long long n_points,
-                            int* status, cudaStream_t st, unsigned long long expire_ns) {
-  if (m > 128 || m < 1) return cudaErrorInvalidValue;
+                            int* status, cudaStream_t st, unsigned long long expire_ns,
+                            int lower) {
+  if (m > 256 || m < 1) return cudaErrorInvalidValue;
   // M hi/lo 128 KB, two X stages 64 KB, output staging 18 KB
   const size_t smem = 2 * (size_t)kMBytes + 4 * (size_t)kXTileBytes + 128 * (kApplyNT + 4) * 4;
   cudaError_t e = cudaFuncSetAttribute(tc_apply_kernel<TX, TY>,
@@ -716,13 +755,24 @@ cudaError_t launch_tc_apply(const double* M, int m, const TX* X, TY* Y, long lon
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long long ntiles = (n_points + kApplyNT - 1) / kApplyNT;
   const int blocks = (int)(ntiles < sms ? ntiles : sms);
-  tc_apply_kernel<TX, TY><<<blocks, kTcThreads, smem, st>>>(M, m, X, Y, n_points, status,
-                                                             expire_ns);
-  return cudaGetLastError();
+  // Y[bi] = sum_bk M[bi][bk] X[bk] (bk <= bi when M is lower triangular),
+  // in stream order: the first block product sets Y[bi], the others add
+  for (int r0 = 0; r0 < m; r0 += 128) {
+    const int nr = m - r0 < 128 ? m - r0 : 128;
+    for (int k0 = 0; k0 < m && (!lower || k0 <= r0); k0 += 128) {
+      const int nk = m - k0 < 128 ? m - k0 : 128;
+      tc_apply_kernel<TX, TY><<<blocks, kTcThreads, smem, st>>>(
+          M, m, r0, nr, k0, nk, k0 > 0, X + (long long)k0 * n_points,
+          Y + (long long)r0 * n_points, n_points, status, expire_ns);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
 }
 
 template cudaError_t launch_tc_apply<float, float>(const double*, int, const float*, float*,
                                                    long long, int*, cudaStream_t,
-                                                   unsigned long long);
+                                                   unsigned long long, int);
 
 }  // namespace itp

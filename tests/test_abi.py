@@ -41,7 +41,7 @@ def test_bad_grid_rejected_before_any_device_call():
         assert ei.value.code == 1
         assert "unsupported grid" in P.itp_last_error(None)
     with pytest.raises(P.ItpError) as ei:
-        P.ItpGrid(32, 32, 32, 10.0, 10.0, 10.0, 200)
+        P.ItpGrid(32, 32, 32, 10.0, 10.0, 10.0, 257)
     assert ei.value.code == 1
 
 

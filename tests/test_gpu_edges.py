@@ -7,7 +7,7 @@ import pytest
 from itp_workloads import Grid
 from oracle import itp_oracle as O
 
-from gpu_helpers import propagate_tolerance, seeded_states, wells_problem
+from gpu_helpers import propagate_tolerance, report, seeded_states, wells_problem
 
 pytestmark = pytest.mark.gpu
 
@@ -17,8 +17,12 @@ PREC = {"fp64": P.ITP_FP64, "mixed": P.ITP_MIXED}
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("m", [1, 128])
+@pytest.mark.parametrize("m", [1, 128, 129, 200, 256])
 def test_state_count_extremes(prec, m):
+    """One state; the largest single 128-state block; and m > 128, where the
+    n x n work runs in 128-state blocks (129: a one-row second block; 256:
+    the largest handle), through propagation, Cholesky orthonormalisation
+    and Ritz values."""
     g = Grid(16, 12, 8, 8.0, 7.0, 6.0)
     V = wells_problem(g)
     psi = seeded_states(g, m)
@@ -33,6 +37,8 @@ def test_state_count_extremes(prec, m):
         got = h.get_states()
     ref = O.propagate(psi, V, g, order, tau)
     err = np.max(np.abs(phi - ref)) / np.max(np.abs(ref))
+    report(f"m={m} {prec} propagate order {order}", err,
+           propagate_tolerance(order, g.n_points, prec))
     assert err < propagate_tolerance(order, g.n_points, prec)
     psi_ref, _ = O.cholesky_orthonormalize(ref, g.dV)
     E_ref, _, _ = O.energies(psi_ref, V, g, ritz=True)
@@ -106,3 +112,34 @@ def test_expired_wait_reports_timeout_and_handle_recovers(which):
             E = h.step_graph(4, 0.2)
             ref, E_ref = O.itp_step(ref, V, g, 4, 0.2)
             assert np.max(np.abs(E - E_ref)) < 1e-5 * np.max(np.abs(E_ref))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("m", [160, 256])
+def test_ritz_rotation_beyond_one_block(prec, m):
+    """The Ritz rotation (parallel Jacobi; above ~166 states its working
+    matrix lives in global memory) and the block-wise update with a full
+    (not triangular) matrix: the Ritz values match the oracle, the rotated
+    states stay orthonormal and diagonalise the subspace matrix, and graph
+    steps continue from them in agreement with the oracle."""
+    g = Grid(24, 16, 12, 9.0, 7.0, 6.0)
+    V = wells_problem(g)
+    psi = seeded_states(g, m, seed=11)
+    with P.ItpGrid(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, m, 0, PREC[prec]) as h:
+        h.set_potential(V)
+        h.set_states(psi)
+        h.propagate(6, 0.1)
+        h.orthonormalize()
+        start = h.get_states()
+        E = h.energies(True)
+        rot = h.get_states()
+        E_diag = h.energies(False)
+        E_next = h.step_graph(6, 0.1)
+    E_ref, _, _ = O.energies(start, V, g, ritz=True)
+    tolE = (1e-11 if prec == "fp64" else 1e-5) * np.max(np.abs(E_ref))
+    assert np.max(np.abs(E - E_ref)) < tolE
+    assert np.max(np.abs(E_diag - E)) < tolE
+    S = rot @ rot.T * g.dV
+    assert np.max(np.abs(S - np.eye(m))) < (1e-11 if prec == "fp64" else 2e-5)
+    _, E_ref2 = O.itp_step(rot, V, g, 6, 0.1)
+    assert np.max(np.abs(E_next - E_ref2)) < tolE

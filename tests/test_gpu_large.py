@@ -11,7 +11,7 @@ import pytest
 from itp_workloads import Grid, c60_like_potential, cubic, normal_states
 from oracle import itp_oracle as O
 
-from gpu_helpers import propagate_tolerance, seeded_states, wells_problem
+from gpu_helpers import propagate_tolerance, report, seeded_states, wells_problem
 
 pytestmark = pytest.mark.gpu
 
@@ -42,6 +42,8 @@ def test_split_plane_step_matches_oracle(dims, prec):
         E = h.energies("values")
         got = h.get_states()
     phi_ref = O.propagate(psi, V, g, order, tau)
+    report(f"{nx}x{ny}x{nz} {prec} propagate order {order} (split planes)",
+           _relerr(phi, phi_ref), propagate_tolerance(order, g.n_points, prec))
     assert _relerr(phi, phi_ref) < propagate_tolerance(order, g.n_points, prec)
     psi_ref, _ = O.cholesky_orthonormalize(phi_ref, g.dV)
     assert _relerr(got, psi_ref) < (1e-11 if prec == "fp64" else 2e-4)
@@ -68,6 +70,7 @@ def test_c60_256_cubed_sampled():
         got = h.get_states()[:2]
     phi_ref = O.propagate(psi[:2], V, g, order, tau)
     tol = propagate_tolerance(order, g.n_points, "mixed")
+    report(f"256^3 mixed propagate order {order} (sampled states)", _relerr(phi, phi_ref), tol)
     assert _relerr(phi, phi_ref) < tol
     psi_ref, _ = O.cholesky_orthonormalize(phi_ref, g.dV)
     # L^{-1} amplifies the error of phi by up to sqrt(cond(S)) of the block

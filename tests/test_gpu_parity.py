@@ -10,7 +10,7 @@ import pytest
 from itp_workloads import Grid, cubic, harmonic_potential
 from oracle import itp_oracle as O
 
-from gpu_helpers import propagate_tolerance, seeded_states, wells_problem
+from gpu_helpers import propagate_tolerance, report, seeded_states, wells_problem
 
 pytestmark = pytest.mark.gpu
 
@@ -52,6 +52,7 @@ def test_propagate_matches_oracle(prec, gi, order):
     ref = O.propagate(psi, V, g, order, tau)
     err = _relerr(phi, ref)
     tol = propagate_tolerance(order, g.n_points, prec)
+    report(f"{g.nx}x{g.ny}x{g.nz} {prec} propagate order {order}", err, tol)
     assert err < tol, (err, tol)
 
 

@@ -10,7 +10,7 @@ import pytest
 from itp_workloads import Grid
 from oracle import itp_oracle as O
 
-from gpu_helpers import propagate_tolerance, seeded_states, wells_problem
+from gpu_helpers import propagate_tolerance, report, seeded_states, wells_problem
 
 pytestmark = pytest.mark.gpu
 
@@ -67,6 +67,8 @@ def test_every_launch_shape_matches_oracle(prec, dims):
                     h.set_states(psi)
                     h.propagate(order, tau)
                     phi = h.get_phi()
+                    report(f"{nx}x{ny}x{nz} {prec} propagate order {order} split={split} "
+                           f"tb={tb} w={w}", _relerr(phi, ref), tol)
                     assert _relerr(phi, ref) < tol, (split, tb, w)
                     h.orthonormalize()
                     got = h.get_states()
@@ -153,6 +155,8 @@ def test_cluster_planes_match_oracle(dims, form):
         h.orthonormalize()
         E = h.energies("values")
     ref = O.propagate(psi, V, g, order, tau)
+    report(f"{nx}x{ny}x{nz} mixed propagate order {order} cluster form {form}",
+           _relerr(phi, ref), propagate_tolerance(order, g.n_points, "mixed"))
     assert _relerr(phi, ref) < propagate_tolerance(order, g.n_points, "mixed")
     psi_ref, _ = O.cholesky_orthonormalize(ref, g.dV)
     E_ref, _, _ = O.energies(psi_ref, V, g, ritz=True)
