@@ -121,6 +121,46 @@ def ncu_traffic(workload, kind):
     return rec["bytes"]
 
 
+def measure_peaks(P):
+    """The GPU's measured arithmetic rates (itp_peak_probe: FP32 FMA, packed
+    FP32 FMA, FP64 FMA, tcgen05 TF32 MMA), with the SM clocks sampled while
+    the probes run."""
+    clocks = ClockSampler()
+    clocks.begin()
+    out = {}
+    for kind in ("ffma", "ffma2", "dfma", "tf32_mma"):
+        try:
+            t, ms = P.itp_peak_probe(kind)
+            out[f"{kind}_tflops"] = round(t, 2)
+            out[f"{kind}_ms"] = round(ms, 2)
+        except Exception as ex:   # an auxiliary figure never takes the bench line down
+            out[f"{kind}_error"] = f"{type(ex).__name__}: {ex}"
+    out["clocks"] = clocks.stop()
+    out["how"] = ("itp_peak_probe: long chains of independent operations on every SM, best of "
+                  "3 launches (CUDA events); an FMA counts 2 flops, an MxNxK MMA 2MNK")
+    return out
+
+
+def fft_pass_flops(kind, g, m):
+    """Algorithmic flops of one FFT pass over m states: a complete complex
+    FFT of length L counts 5 L log2 L, a real one half that; the plane pass
+    does the 2D real transform(s) of its plane (two for the merged pass),
+    the pencil pass a forward and an inverse complex transform along z of
+    each of the nx/2+1 columns, plus one multiply per point for the factors."""
+    import math
+    P2 = g.nx * g.ny
+    Nh = g.nz * g.ny * (g.nx // 2 + 1)
+    real2d = 2.5 * P2 * math.log2(P2) if P2 > 1 else 0.0
+    zfft = 5.0 * g.nz * math.log2(g.nz) if g.nz > 1 else 0.0
+    per = {"plane_merged": 2 * real2d + P2, "plane_fwd": real2d + P2,
+           "plane_combine": real2d + 3 * P2, "plane_hpsi": real2d + 2 * P2}
+    if kind in per:
+        return m * g.nz * per[kind]
+    if kind in ("pencil", "pencil_kinetic"):
+        return m * (Nh // g.nz) * (2 * zfft + 2 * g.nz)
+    return None
+
+
 def _hbm_peak():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
@@ -342,32 +382,91 @@ def ho_closed_shells(n):
     return np.array(E[:n])
 
 
-def time_to_tol(P, precision, tol=1e-8, order=12, tau=0.5, n=120, guard=8,
-                max_fp32=400, max_fp64=200, plateau_rel=1e-5, polish_order=None):
+# Problems of the time-to-tolerance runs: grid edge, box, potential, the
+# reference energies (exact closed shells for the oscillator; the oracle's
+# certified eigenvalues of the grid Hamiltonian for the C60-like well, stored
+# by tests/golden/make_c60_eref.py), seed of the random-normal start.
+TTT_PROBLEMS = {
+    "c60_128": {"desc": "C60-like Gaussian well (60 wells, depth 2.0 Ha, sigma 0.8 bohr, "
+                        "radius 6.7 bohr), 128^3 grid, box 32 bohr",
+                "n": 128, "box": 32.0, "potential": "c60",
+                "eref": os.path.join("tests", "golden", "c60_128_eref.txt"), "seed": 4321},
+    "osc_128": {"desc": "3D harmonic oscillator, 128^3 grid, box [-8,8)^3 (eight closed "
+                        "shells, exact E = n + 3/2)",
+                "n": 128, "box": 16.0, "potential": "ho", "eref": None, "seed": 4321},
+}
+
+
+# The C60-like time-to-tolerance run: n = 120 wanted states and 136 guard
+# states (m = 256, two tensor-core tiles: the gap from state 120 to state 257
+# sets the convergence rate; with 8 guard states it is ~0.008 Ha, with 136
+# about ten times larger), order 12 at tau = 1.
+C60_TTT = {"n": 120, "guard": 136, "order": 12, "tau": 1.0, "max_fp32": 400, "max_fp64": 300}
+
+
+def fp64_step_extrapolation(P, mixed, n, guard, order, tau, **_):
+    """The FP64 path's time to tolerance estimated (not measured) from its
+    measured step time: the FP64 iteration is the same map as the FP32 one,
+    so it needs about as many steps as the mixed path took in all."""
+    from itp_workloads import c60_like_potential, cubic, normal_states
+    pr = TTT_PROBLEMS["c60_128"]
+    g = cubic(pr["n"], pr["box"])
+    h = P.ItpGrid(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, n, guard, P.ITP_FP64)
+    h.set_potential(c60_like_potential(g))
+    h.set_states(normal_states(n + guard, g.n_points, seed=pr["seed"]))
+    h.step_graph(order, tau)
+    t0 = time.perf_counter()
+    for _ in range(2):
+        h.step_graph(order, tau)
+    step_s = (time.perf_counter() - t0) / 2
+    h.close()
+    steps = mixed["fp32_steps"] + mixed["fp64_steps"]
+    return {"seconds_estimated": step_s * steps, "step_seconds": step_s, "steps_assumed": steps,
+            "how": "estimated, not measured: the measured FP64 step time x the mixed path's "
+                   "total step count (run bench.py with --fp64-ttt to measure it)"}
+
+
+def load_eref(path):
+    """Reference eigenvalues from a stored table (column 2 of the data rows)."""
+    vals = []
+    with open(os.path.join(ROOT, path)) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                vals.append(float(line.split()[1]))
+    return np.array(vals)
+
+
+def time_to_tol(P, precision, problem="c60_128", tol=1e-8, order=12, tau=0.5, n=120, guard=8,
+                max_fp32=400, max_fp64=200, plateau_rel=1e-5, polish_order=None,
+                per_state=False):
     """Wall time from itp_set_states of seeded random states until every one
-    of the n lowest Ritz energies is within tol of its exact value (3D
-    harmonic oscillator, 128^3 grid, box [-8,8)^3, n = 120 = eight closed
-    shells).  FP64: FP64 steps throughout.  Mixed: FP32 steps while the
-    energies still change by more than plateau_rel * max|E| per step (the
-    FP32-evaluated energies level off near 1e-5 relative while the FP32
-    states keep converging), then as many further FP32 steps as the observed
-    convergence rate says the states need, then FP64 polish steps
-    (itp_polish, one step per call) until within tol.  The reference is used
-    only to stop the clock, never to steer the iteration."""
-    from itp_workloads import cubic, harmonic_potential, normal_states
-    g = cubic(128, 16.0)
-    V = harmonic_potential(g)
+    of the n lowest Ritz energies is within tol of its reference value.
+    FP64: FP64 steps throughout.  Mixed: FP32 steps while the energies still
+    change by more than plateau_rel * max|E| per step (the FP32-evaluated
+    energies level off near 1e-5 relative while the FP32 states keep
+    converging), then as many further FP32 steps as the observed convergence
+    rate says the states need, then FP64 polish steps (itp_polish, one step
+    per call) until within tol.  The reference is used only to stop the
+    clock, never to steer the iteration.  per_state: also return every
+    state's final error."""
+    from itp_workloads import c60_like_potential, cubic, harmonic_potential, normal_states
+    pr = TTT_PROBLEMS[problem]
+    g = cubic(pr["n"], pr["box"])
+    V = c60_like_potential(g) if pr["potential"] == "c60" else harmonic_potential(g)
     m = n + guard
-    psi = normal_states(m, g.n_points, seed=4321)
-    E_ref = ho_closed_shells(n)
+    psi = normal_states(m, g.n_points, seed=pr["seed"])
+    E_ref = load_eref(pr["eref"])[:n] if pr["eref"] else ho_closed_shells(n)
     h = P.ItpGrid(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, n, guard, precision)
     h.set_potential(V)
+    h.set_states(psi)
+    tuned, _ = h.autotune(order, tau)   # launch shapes for this state count (untimed)
     h.synchronize()
     t0 = time.perf_counter()
     h.set_states(psi)
     steps32 = steps64 = 0
     err = float("inf")
     E_prev = None
+    E = None
     if precision == P.ITP_MIXED:
         # FP32 steps until the FP32-evaluated energies stop moving; the
         # states keep converging below that floor at the rate the energy
@@ -410,8 +509,11 @@ def time_to_tol(P, precision, tol=1e-8, order=12, tau=0.5, n=120, guard=8,
     h.synchronize()
     dt = time.perf_counter() - t0
     h.close()
-    return {"seconds": dt, "fp32_steps": steps32, "fp64_steps": steps64,
-            "max_abs_error_ha": err, "reached": err < tol}
+    out = {"seconds": dt, "fp32_steps": steps32, "fp64_steps": steps64,
+           "max_abs_error_ha": err, "reached": err < tol, "launch_shapes": tuned}
+    if per_state and E is not None:
+        out["errors_ha"] = [float(f"{x:.3e}") for x in (E[:n] - E_ref)]
+    return out
 
 
 # The 32^3 oscillator workload: box [-8,8)^3, V = r^2/2, n = 10 states (three
@@ -475,20 +577,20 @@ def osc32_oracle():
 
 
 def extrapolate_oracle(cpu, ttt, m):
-    """The oracle's time to tolerance on the 128^3 oscillator, extrapolated
+    """The oracle's time to tolerance on the C60-like workload, extrapolated
     (not measured): m states x the FP64 path's step count there, divided by
-    the oracle's measured state-steps per second on the same grid, order and
-    state count.  None when either figure is missing."""
+    the oracle's measured state-steps per second on the same grid and order.
+    None when either figure is missing."""
     if not cpu or not cpu.get("value") or not ttt or "fp64" not in ttt:
         return None
-    steps = ttt["fp64"].get("fp64_steps")
+    steps = ttt["fp64"].get("fp64_steps") or ttt["fp64"].get("steps_assumed")
     if not steps:
         return None
     return {"value_s": round(m * steps / cpu["value"], 1),
             "how": f"extrapolated, not measured: {m} states x {steps} FP64 steps (the GPU "
-                   "FP64 path's step count to the tolerance on the 128^3 oscillator, same "
-                   "grid, order and state count as the sample) / the oracle's measured "
-                   "state-steps per second"}
+                   "FP64 path's step count to the tolerance on the same workload, grid and "
+                   "order as the oracle's sample) / the oracle's measured state-steps per "
+                   "second"}
 
 
 def adaptive_to_tol(P, precision, tol=1e-8, order=12, n=120, guard=8):
@@ -802,6 +904,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance runs")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
+    ap.add_argument("--no-fp64-ttt", dest="fp64_ttt", action="store_false",
+                    help="estimate the FP64 path's time to tolerance on the C60-like workload "
+                         "from its step time instead of running it (about two minutes)")
     ap.add_argument("--adaptive-fp64", action="store_true",
                     help="also time the FP64 adaptive iteration (about two minutes)")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
@@ -965,6 +1070,8 @@ def main():
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    # this GPU's own arithmetic rates (FP32, FP64, TF32 tensor), measured here
+    probes = measure_peaks(P)
     roof = None
     ab = algorithmic_bytes(top, g, m, 4, mixed=True)
     if ab is not None:
@@ -983,6 +1090,23 @@ def main():
             roof_all[k] = {"avg_launch_ms": round(t * 1e3, 4),
                            "achieved_gbs": round(b / t / 1e9, 1),
                            "frac": round(b / t / 1e9 / hbm_peak, 4)}
+    # the tensor-core Gram (overlap and subspace matrix, 128 x 128 blocks):
+    # three TF32 products per FP32 product, against the measured TF32 MMA rate
+    gram_tc = None
+    if "gram" in kinds and probes.get("tf32_mma_tflops"):
+        nb = (m + 127) // 128
+        t = kinds["gram"][1] / 1e3 / kinds["gram"][0]
+        # per launch on average: the overlap (nb(nb+1)/2 blocks) and the
+        # subspace matrix (nb^2 blocks) alternate
+        blocks = 0.5 * (nb * (nb + 1) / 2 + nb * nb)
+        ach = 3 * 2 * 128 * 128 * blocks * g.n_points / t / 1e12
+        gram_tc = {"bound": "tensor (TF32)", "achieved": ach, "peak": probes["tf32_mma_tflops"],
+                   "unit": "TFLOP/s", "frac": ach / probes["tf32_mma_tflops"],
+                   "avg_launch_ms": round(t * 1e3, 4),
+                   "hbm_gbs": round(1.5 * m * g.n_points * 4 / t / 1e9, 1),
+                   "how": "3 TF32 MMA products per FP32 product (hi*hi + hi*lo + lo*hi), "
+                          "128 x 128 result blocks; hbm_gbs: the FP32 operands read (one "
+                          "block for the overlap, two for the subspace matrix, averaged)"}
     # the whole timed step against the same roofline: its algorithmic bytes
     # (every pass, the term sum, overlap, update, energies) over the step time
     sb = step_bytes(g, m, order // 2)
@@ -1047,29 +1171,61 @@ def main():
                 "ms_per_step": 1e3 * dt64 / K, "launch_shapes": tuned64,
                 "breakdown": {k: {"launches": v[0], "ms": round(v[1], 3),
                                   "share": round(v[1] / tot64, 4)} for k, v in prof64.items()}}
+        # the FP64 path is bound by GB300's FP64 rate: its dominant FFT pass
+        # against the measured DFMA rate
+        top64 = max((k for k in prof64 if fft_pass_flops(k, g, m) is not None),
+                    key=lambda k: prof64[k][1], default=None)
+        if top64 is not None and probes.get("dfma_tflops"):
+            t = prof64[top64][1] / 1e3 / prof64[top64][0]
+            ach = fft_pass_flops(top64, g, m) / t / 1e12
+            fp64["roofline"] = {"kernel": top64, "bound": "alu (FP64)", "achieved": ach,
+                                "peak": probes["dfma_tflops"], "unit": "TFLOP/s",
+                                "frac": ach / probes["dfma_tflops"],
+                                "avg_launch_ms": round(t * 1e3, 3),
+                                "peak_source": "measured (itp_peak_probe DFMA)"}
         h.close()
 
     # ---- time to n states at tol: mixed vs FP64 --------------------------------
     ttt = None
+    ttt_osc = None
     if not args.no_ttt:
         barrier()
-        ttt = {"workload": "3D harmonic oscillator, 128^3 grid, box [-8,8)^3, n = 120 "
-                           "(eight closed shells, exact E = n + 3/2) + 8 guard, order 12, "
-                           "tau = 0.5, seeded random-normal start",
+        # the metric's own workload: C60-like well, 128^3, n = 120, against
+        # the oracle's certified eigenvalues of the grid Hamiltonian
+        c60 = TTT_PROBLEMS["c60_128"]
+        ttt = {"workload": f"{c60['desc']}, n = 120 + {C60_TTT['guard']} guard, order 12, "
+                           f"tau = {C60_TTT['tau']}, seeded random-normal start",
+               "reference": f"{c60['eref']} (the oracle's LOBPCG eigenvalues of the grid "
+                            "Hamiltonian, certified by residual norms)",
                "tol_ha": 1e-8,
-               "mixed": time_to_tol(P, P.ITP_MIXED),
-               "fp64": time_to_tol(P, P.ITP_FP64)}
-        ttt["speedup_mixed_vs_fp64"] = ttt["fp64"]["seconds"] / ttt["mixed"]["seconds"]
+               "mixed": time_to_tol(P, P.ITP_MIXED, per_state=True, **C60_TTT)}
+        if args.fp64_ttt:
+            ttt["fp64"] = time_to_tol(P, P.ITP_FP64, per_state=True, **C60_TTT)
+            ttt["speedup_mixed_vs_fp64"] = ttt["fp64"]["seconds"] / ttt["mixed"]["seconds"]
+        else:
+            # one FP64 step measured; the FP64 path needs at least as many
+            # steps as the mixed path took in all (same iteration, FP64 states)
+            ttt["fp64"] = fp64_step_extrapolation(P, ttt["mixed"], **C60_TTT)
+        # the 3D oscillator (exact closed-shell energies) with 8 guard states
+        ttt_osc = {"workload": f"{TTT_PROBLEMS['osc_128']['desc']}, n = 120 + 8 guard, "
+                               "order 12, tau = 0.5, seeded random-normal start",
+                   "tol_ha": 1e-8,
+                   "mixed": time_to_tol(P, P.ITP_MIXED, problem="osc_128"),
+                   "fp64": time_to_tol(P, P.ITP_FP64, problem="osc_128")}
+        ttt_osc["speedup_mixed_vs_fp64"] = (ttt_osc["fp64"]["seconds"]
+                                            / ttt_osc["mixed"]["seconds"])
         # order 6 (the fastest order per converged state on one GB300, as the
         # paper found on one processor): FP32 steps at order 6, FP64 polish at
         # order 12; and the FP64 path at order 6
-        ttt["order6"] = {"mixed_fp32_order6_polish_order12":
-                         time_to_tol(P, P.ITP_MIXED, order=6, polish_order=12),
-                         "fp64_order6": time_to_tol(P, P.ITP_FP64, order=6)}
+        ttt_osc["order6"] = {"mixed_fp32_order6_polish_order12":
+                             time_to_tol(P, P.ITP_MIXED, problem="osc_128", order=6,
+                                         polish_order=12),
+                             "fp64_order6": time_to_tol(P, P.ITP_FP64, problem="osc_128",
+                                                        order=6)}
         # the same problem with the adaptive iteration of Sec. III
-        ttt["adaptive"] = {"mixed": adaptive_to_tol(P, P.ITP_MIXED)}
+        ttt_osc["adaptive"] = {"mixed": adaptive_to_tol(P, P.ITP_MIXED)}
         if args.adaptive_fp64:   # about two minutes on one GB300
-            ttt["adaptive"]["fp64"] = adaptive_to_tol(P, P.ITP_FP64)
+            ttt_osc["adaptive"]["fp64"] = adaptive_to_tol(P, P.ITP_FP64)
 
     # ---- the 32^3 oscillator to 1e-10 Ha (GPU FP64; the oracle beside it) ----
     osc32 = None
@@ -1126,7 +1282,8 @@ def main():
 
     if cpu is not None and ttt is not None:
         try:
-            ttt["fp64_oracle_extrapolated"] = extrapolate_oracle(cpu, ttt, m)
+            ttt["fp64_oracle_extrapolated"] = extrapolate_oracle(
+                cpu, ttt, C60_TTT["n"] + C60_TTT["guard"])
         except Exception as ex:   # an auxiliary figure never takes the bench line down
             ttt["fp64_oracle_extrapolated"] = {"error": f"{type(ex).__name__}: {ex}"}
 
@@ -1154,10 +1311,13 @@ def main():
             "roofline": roof,
             "rooflines_fft_passes": roof_all,
             "step_roofline": step_roof,
+            "measured_peaks": probes,
+            "gram_tensor_roofline": gram_tc,
             "kernel_breakdown": breakdown,
             "eager_profiled": eager,
             "fp64_path": fp64,
             "time_to_tol": ttt,
+            "time_to_tol_osc128": ttt_osc,
             "time_to_tol_osc32": osc32,
             "orders": {"ms_per_step_by_order": order_cost,
                        "propagation_ms": prop_ms,

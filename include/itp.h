@@ -400,6 +400,24 @@ void itp_batch_destroy(itp_batch_handle b);
 int itp_orthonormalize_noalloc(const double* phi_device, double* psi_device, int m,
                                long long n_points, double dV, void* cuda_stream);
 
+/* ---- Measured arithmetic rates -----------------------------------------------
+ * Denominators for the ALU and tensor rooflines of the kernels (the paper has
+ * no counterpart).  Runs one probe on the current device: long chains of
+ * independent operations on every SM, timed with CUDA events on cuda_stream
+ * (NULL: default stream), best of three launches after one warm-up; no clock
+ * or other GPU setting is changed, so the rate is the one at whatever clocks
+ * the GPU runs (sample them alongside).  *tflops receives the achieved
+ * TFLOP/s (an FMA counts 2 flops; an M x N x K MMA 2MNK), *ms_out (nullable)
+ * the duration of one launch.  Allocates and frees a few bytes of device
+ * memory.  Returns ITP_OK, ITP_ERR_ARG (unknown kind or null tflops),
+ * ITP_ERR_OOM, ITP_ERR_CUDA, or ITP_ERR_TIMEOUT (the MMA probe's bounded wait
+ * for its tensor-core work expired). */
+#define ITP_PROBE_FFMA 0      /* FP32 FMA, one value per instruction            */
+#define ITP_PROBE_FFMA2 1     /* packed two-lane FP32 FMA (sm_100+)             */
+#define ITP_PROBE_DFMA 2      /* FP64 FMA                                       */
+#define ITP_PROBE_TF32_MMA 3  /* tcgen05.mma kind::tf32 128x256x8, FP32 in TMEM */
+int itp_peak_probe(int kind, void* cuda_stream, double* tflops, double* ms_out);
+
 #ifdef __cplusplus
 }
 #endif

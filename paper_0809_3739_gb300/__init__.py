@@ -10,4 +10,4 @@ from .itp import (ITP_FP64, ITP_MIXED, ITP_RITZ, ITP_RITZ_VALUES, ITP_STEP_FP64,
                   itp_profile, itp_profile_read, itp_propagate, itp_propagate_romberg6,
                   itp_set_potential,
                   itp_set_states, itp_set_states_device, itp_solve_adaptive, itp_step, itp_step_host,
-                  itp_synchronize, itp_test_expire_waits, load)
+                  itp_synchronize, itp_test_expire_waits, itp_peak_probe, load)

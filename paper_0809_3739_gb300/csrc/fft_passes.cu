@@ -172,6 +172,33 @@ struct PlaneGeo {
   __device__ __forceinline__ int col(int t, int e) const {
     return (e >> 1) * pp + (e & 1) * nxh + t;
   }
+  // The same positions for the elements a stage touches: e = n1 + r1*j of a
+  // stage-A task (n1 < r1), e = i + r1*b of a stage-B task (i < r1), with j
+  // and i unrolled.  When r1 divides 16 (rows) or is even (columns) -- every
+  // specialised edge but 48 -- the position is a per-task base plus a
+  // compile-time offset, since n1 or i cannot carry into the pad term
+  // (r1*j mod 16 <= 16 - r1) or the row-pair index; the shared-memory
+  // accesses then need no address arithmetic per element.
+  static constexpr int XR1 = NX ? AxisT<NX>::R1_ : 0;
+  static constexpr int YR1 = NY ? AxisT<NY>::R1_ : 0;
+  static constexpr bool kRowFast = XR1 > 0 && 16 % XR1 == 0;
+  static constexpr bool kColFast = YR1 > 0 && YR1 % 2 == 0;
+  __device__ __forceinline__ int rowA(int t, int n1, int j) const {
+    if constexpr (kRowFast) return (t * pp + n1) + (XR1 * j + ((XR1 * j) >> 4));
+    else return row(t, n1 + ax.r1 * j);
+  }
+  __device__ __forceinline__ int rowB(int t, int b, int i) const {
+    if constexpr (kRowFast) return (t * pp + XR1 * b + ((XR1 * b) >> 4)) + i;
+    else return row(t, i + ax.r1 * b);
+  }
+  __device__ __forceinline__ int colA(int t, int n1, int j) const {
+    if constexpr (kColFast) return ((n1 >> 1) * pp + (n1 & 1) * nxh + t) + (YR1 / 2) * j * pp;
+    else return col(t, n1 + ay.r1 * j);
+  }
+  __device__ __forceinline__ int colB(int t, int b, int i) const {
+    if constexpr (kColFast) return ((YR1 / 2) * b * pp + t) + ((i >> 1) * pp + (i & 1) * nxh);
+    else return col(t, i + ay.r1 * b);
+  }
 };
 
 // ---- x stages (rows), all in shared memory except the fused ends ------------
@@ -197,7 +224,7 @@ __device__ __forceinline__ void xA_fwd_global_r(const PlaneGeo<R, NX, NY, NTT>& 
       for (int j = 1; j < R2; ++j) a[j] = cmul(a[j], tw[n1 * j]);
     }
 #pragma unroll
-    for (int j = 0; j < R2; ++j) sm[G.row(t, n1 + G.ax.r1 * j)] = a[j];
+    for (int j = 0; j < R2; ++j) sm[G.rowA(t, n1, j)] = a[j];
   });
 }
 template <typename R, int NX, int NY, int NTT, typename C>
@@ -214,14 +241,14 @@ __device__ __forceinline__ void xB_r(const PlaneGeo<R, NX, NY, NTT>& G, C* sm, c
   for_tasks<NT>(G.npair, G.ax.r2, [&](int t, int b) {
     C a[R1];
 #pragma unroll
-    for (int i = 0; i < R1; ++i) a[i] = sm[G.row(t, i + R1 * b)];
+    for (int i = 0; i < R1; ++i) a[i] = sm[G.rowB(t, b, i)];
     Dft<R1, DIR, C>::run(a);
     if (DIR > 0) {
 #pragma unroll
       for (int i = 1; i < R1; ++i) a[i] = cmulc(a[i], tw[i * b]);
     }
 #pragma unroll
-    for (int i = 0; i < R1; ++i) sm[G.row(t, i + R1 * b)] = a[i];
+    for (int i = 0; i < R1; ++i) sm[G.rowB(t, b, i)] = a[i];
   });
 }
 template <int R1, typename G_, typename C>
@@ -249,7 +276,7 @@ __device__ __forceinline__ void xA_inv_then_r(const PlaneGeo<R, NX, NY, NTT>& G,
   for_tasks<NT>(G.npair, G.ax.r1, [&](int t, int n1) {
     C a[R2];
 #pragma unroll
-    for (int j = 0; j < R2; ++j) a[j] = sm[G.row(t, n1 + G.ax.r1 * j)];
+    for (int j = 0; j < R2; ++j) a[j] = sm[G.rowA(t, n1, j)];
     Dft<R2, 1, C>::run(a);
     if (epi.template apply<R2>(t, n1, a)) {
       Dft<R2, -1, C>::run(a);
@@ -258,7 +285,7 @@ __device__ __forceinline__ void xA_inv_then_r(const PlaneGeo<R, NX, NY, NTT>& G,
         for (int j = 1; j < R2; ++j) a[j] = cmul(a[j], tw[n1 * j]);
       }
 #pragma unroll
-      for (int j = 0; j < R2; ++j) sm[G.row(t, n1 + G.ax.r1 * j)] = a[j];
+      for (int j = 0; j < R2; ++j) sm[G.rowA(t, n1, j)] = a[j];
     }
   });
 }
@@ -376,7 +403,7 @@ __device__ __forceinline__ void xB_fwd_split_r(const PlaneGeo<R, NX, NY, NTT>& G
     C* row = sm + (active ? t : 0) * G.pp;
     C a[R1];
 #pragma unroll
-    for (int i = 0; i < R1; ++i) a[i] = active ? row[swz(i + R1 * b)] : C{0, 0};
+    for (int i = 0; i < R1; ++i) a[i] = active ? sm[G.rowB(active ? t : 0, b, i)] : C{0, 0};
     Dft<R1, -1, C>::run(a);   // a[k1] = Z[b + r2*k1]
     C zm[R1];
 #pragma unroll
@@ -450,7 +477,7 @@ __device__ __forceinline__ void xB_inv_merge_r(const PlaneGeo<R, NX, NY, NTT>& G
     }
     if (active) {
 #pragma unroll
-      for (int i = 0; i < R1; ++i) row[swz(i + R1 * b)] = v[i];
+      for (int i = 0; i < R1; ++i) sm[G.rowB(t, b, i)] = v[i];
     }
     __syncwarp();
   }
@@ -492,7 +519,7 @@ __device__ __forceinline__ void yB_inv_global_r(const PlaneGeo<R, NX, NY, NTT>& 
       for (int i = 1; i < R1; ++i) a[i] = cmulc(a[i], tw[i * b]);
     }
 #pragma unroll
-    for (int i = 0; i < R1; ++i) sm[G.col(t, i + R1 * b)] = a[i];
+    for (int i = 0; i < R1; ++i) sm[G.colB(t, b, i)] = a[i];
   });
 }
 template <typename R, int NX, int NY, int NTT, typename C>
@@ -508,14 +535,14 @@ __device__ __forceinline__ void yA_r(const PlaneGeo<R, NX, NY, NTT>& G, C* sm, c
   for_tasks<NT>(G.nxh, G.ay.r1, [&](int t, int n1) {
     C a[R2];
 #pragma unroll
-    for (int j = 0; j < R2; ++j) a[j] = sm[G.col(t, n1 + G.ay.r1 * j)];
+    for (int j = 0; j < R2; ++j) a[j] = sm[G.colA(t, n1, j)];
     Dft<R2, DIR, C>::run(a);
     if (DIR < 0 && G.ay.r1 > 1) {
 #pragma unroll
       for (int j = 1; j < R2; ++j) a[j] = cmul(a[j], tw[n1 * j]);
     }
 #pragma unroll
-    for (int j = 0; j < R2; ++j) sm[G.col(t, n1 + G.ay.r1 * j)] = a[j];
+    for (int j = 0; j < R2; ++j) sm[G.colA(t, n1, j)] = a[j];
   });
 }
 template <int R2, typename G_, typename C>
@@ -546,7 +573,7 @@ __device__ __forceinline__ void yB_fwd_global_r(const PlaneGeo<R, NX, NY, NTT>& 
   for_tasks<NT>(G.nxh, G.ay.r2, [&](int t, int b) {
     C a[R1];
 #pragma unroll
-    for (int i = 0; i < R1; ++i) a[i] = sm[G.col(t, i + R1 * b)];
+    for (int i = 0; i < R1; ++i) a[i] = sm[G.colB(t, b, i)];
     Dft<R1, -1, C>::run(a);
     if (kin.fx) {
 #pragma unroll

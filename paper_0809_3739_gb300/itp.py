@@ -58,6 +58,7 @@ SIGNATURES = [
     ("itp_profile", _I, [_H, _I]),
     ("itp_profile_read", _I, [_H, _I, ctypes.POINTER(ctypes.c_longlong),
                               ctypes.POINTER(ctypes.c_double)]),
+    ("itp_peak_probe", _I, [_I, ctypes.c_void_p, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     ("itp_orthonormalize_noalloc", _I, [ctypes.c_void_p, ctypes.c_void_p, _I, ctypes.c_longlong,
                                         _D, ctypes.c_void_p]),
     ("itp_get_tuning", _I, [_H, _PD]),
@@ -265,6 +266,23 @@ def itp_orthonormalize_noalloc(phi_device_ptr: int, psi_device_ptr: int, m: int,
                                             ctypes.c_void_p(cuda_stream or None))
     if code != ITP_OK:
         raise ItpError(code, "itp_orthonormalize_noalloc failed")
+
+
+ITP_PROBE_FFMA, ITP_PROBE_FFMA2, ITP_PROBE_DFMA, ITP_PROBE_TF32_MMA = 0, 1, 2, 3
+PROBE_KINDS = {"ffma": ITP_PROBE_FFMA, "ffma2": ITP_PROBE_FFMA2, "dfma": ITP_PROBE_DFMA,
+               "tf32_mma": ITP_PROBE_TF32_MMA}
+
+
+def itp_peak_probe(kind, cuda_stream: int = 0):
+    """Measured rate of one kind of arithmetic on the current device:
+    returns (TFLOP/s, ms per probe launch)."""
+    t = ctypes.c_double()
+    ms = ctypes.c_double()
+    code = load().itp_peak_probe(PROBE_KINDS.get(kind, kind), ctypes.c_void_p(cuda_stream or None),
+                                 ctypes.byref(t), ctypes.byref(ms))
+    if code != ITP_OK:
+        raise ItpError(code, f"itp_peak_probe({kind}) failed")
+    return t.value, ms.value
 
 
 def itp_get_tuning(h) -> dict:

@@ -1,12 +1,17 @@
 """Shared helpers of the GPU tests: seeded problems and the tolerances.
 
-Tolerances (derived from the arithmetic, stated once here):
-  a complete 3D FFT (forward + inverse) in precision eps has a relative
-  rounding error of about eps * log2(N); term i of the order-2k expansion
-  applies i of them and is scaled by |c_i|, so the propagated block carries
-  an error of about  eps * log2(N) * sum_i i |c_i|  relative to the largest
-  value.  The tests allow 8x that (FP64) and 2x (FP32, where the bound is
-  already pessimistic because the terms' errors are independent).
+Tolerance of the propagated block (derived from the arithmetic, stated
+once here, and checked against the errors every GPU test prints):
+  the rounding errors of a complete 3D FFT pair in precision eps are many
+  independent roundings, so they grow like a random walk, about
+  eps * sqrt(log2 N) relative to the largest value; term i of the order-2k
+  expansion applies i such pairs and is scaled by c_i, and the terms'
+  errors are independent, so they add in quadrature:
+      e(order, N) = eps * sqrt(log2 N) * sqrt(sum_i i c_i^2).
+  Across every grid, order, precision, launch shape and state count the
+  tests run (48 to 256 per edge, 1 to 256 states, orders 2-12) the observed
+  maximum error is 0.5 - 2.0 e (FP64) and 0.5 - 1.25 e (mixed); the tests
+  allow 4 e.
 """
 import math
 
@@ -21,11 +26,9 @@ EPS32 = 2.0 ** -24
 
 def propagate_tolerance(order: int, n_points: int, precision: str) -> float:
     c = O.mp_coefficients_float(order // 2)
-    weight = sum((i + 1) * abs(ci) for i, ci in enumerate(c))
-    lg = math.log2(n_points)
-    if precision == "fp64":
-        return max(8 * EPS64 * lg * weight, 1e-13)
-    return 2 * EPS32 * lg * weight + 1e-6
+    weight = math.sqrt(sum((i + 1) * ci * ci for i, ci in enumerate(c)))
+    eps = EPS64 if precision == "fp64" else EPS32
+    return 4 * eps * math.sqrt(math.log2(n_points)) * weight
 
 
 def wells_problem(g: Grid, n_wells: int = 5, seed: int = 3):
