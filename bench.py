@@ -50,6 +50,12 @@ WORKLOADS = {
                         tau=0.25, seed=1234,
                         desc="C60-like Gaussian well, 128^3 grid, box 32 bohr, 16 states, "
                              "order 12, tau = 0.25 (profiling case)"),
+    # 128 states on a 64^3 grid: the tensor-core kernels' full tile height with
+    # a state block (134 MB FP32) just above L2, small enough for full ncu captures
+    "c60_64_m128": dict(n=64, box=32.0, potential="c60", n_states=120, n_guard=8, order=12,
+                        tau=0.25, seed=1234,
+                        desc="C60-like Gaussian well, 64^3 grid, box 32 bohr, 120 + 8 states, "
+                             "order 12, tau = 0.25 (profiling case of the tensor-core kernels)"),
     "ho_32": dict(n=32, box=16.0, potential="ho", n_states=10, n_guard=2, order=4, tau=0.1,
                   seed=1234, desc="3D harmonic oscillator, 32^3 grid, box [-8,8)^3, n=10 + 2 "
                                   "guard, order 4, tau = 0.1"),
@@ -78,9 +84,9 @@ NCU_TRAFFIC = {
     # DRAM bytes (read + write) per full launch from one ncu capture of the
     # 16-state case, scaled by the number of states; valid only while the
     # kernel's source file is the one that was profiled
-    ("c60_128", "plane_merged"): {"bytes": 1.796e9,
+    ("c60_128", "plane_merged"): {"bytes": 1.791e9,
                                   "source": "paper_0809_3739_gb300/csrc/fft_passes.cu",
-                                  "sha1": "4b63d6767e836d25c60d7178d2f84d0b67ddf33e",
+                                  "sha1": "3663773ba8b725bbf787510fb6e3647e00cbbbdf",
                                   "profile": "profiles/plane_merged_c60_128.md"},
     ("c60_128", "pencil"): {"bytes": 1.718e9,
                             "source": "paper_0809_3739_gb300/csrc/fft_passes.cu",
@@ -438,7 +444,7 @@ def load_eref(path):
 
 def time_to_tol(P, precision, problem="c60_128", tol=1e-8, order=12, tau=0.5, n=120, guard=8,
                 max_fp32=400, max_fp64=200, plateau_rel=1e-5, polish_order=None,
-                per_state=False):
+                per_state=False, fp64_eval=False, margin=1.0):
     """Wall time from itp_set_states of seeded random states until every one
     of the n lowest Ritz energies is within tol of its reference value.
     FP64: FP64 steps throughout.  Mixed: FP32 steps while the energies still
@@ -446,9 +452,11 @@ def time_to_tol(P, precision, problem="c60_128", tol=1e-8, order=12, tau=0.5, n=
     energies level off near 1e-5 relative while the FP32 states keep
     converging), then as many further FP32 steps as the observed convergence
     rate says the states need, then FP64 polish steps (itp_polish, one step
-    per call) until within tol.  The reference is used only to stop the
-    clock, never to steer the iteration.  per_state: also return every
-    state's final error."""
+    per call) until within tol.  fp64_eval: before any polish step, the
+    final energy evaluation in FP64 (ITP_EVAL_FP64), with ten more FP32 steps
+    before each further one; margin: the FP32 phase aims its extra steps at
+    tol / margin.  The reference is used only to stop the clock, never to
+    steer the iteration.  per_state: also return every state's final error."""
     from itp_workloads import c60_like_potential, cubic, harmonic_potential, normal_states
     pr = TTT_PROBLEMS[problem]
     g = cubic(pr["n"], pr["box"])
@@ -463,7 +471,7 @@ def time_to_tol(P, precision, problem="c60_128", tol=1e-8, order=12, tau=0.5, n=
     h.synchronize()
     t0 = time.perf_counter()
     h.set_states(psi)
-    steps32 = steps64 = 0
+    steps32 = steps64 = evals = 0
     err = float("inf")
     E_prev = None
     E = None
@@ -491,12 +499,26 @@ def time_to_tol(P, precision, problem="c60_128", tol=1e-8, order=12, tau=0.5, n=
                     clean = [d for d in dEs[-4:] if d > 0]
                     rates = [b / a for a, b in zip(clean, clean[1:]) if a > 0]
                     rho = min(0.9, max(0.05, float(np.median(rates)))) if rates else 0.5
-                    extra = int(np.ceil(np.log(max(dEs[-1], tol) / tol) / np.log(1.0 / rho)))
+                    goal = tol / margin
+                    extra = int(np.ceil(np.log(max(dEs[-1], goal) / goal) / np.log(1.0 / rho)))
                     extra = min(extra, 60)
                     if extra <= 0:
                         break
                 dEs.append(dE)
             E_prev = E
+        if fp64_eval:
+            # the final evaluation in FP64 (ITP_EVAL_FP64: no FP64
+            # propagation); if the states were not yet converged, ten more
+            # FP32 steps before each further evaluation
+            while evals < 10:
+                E = h.energies("values", fp64=True)
+                evals += 1
+                err = float(np.max(np.abs(E[:n] - E_ref)))
+                if err < tol:
+                    break
+                for _ in range(10):
+                    h.step_graph(order, tau)
+                    steps32 += 1
         while err >= tol and steps64 < max_fp64:
             _, E = h.polish(polish_order or order, tau, 1e-300, 1)
             steps64 += 1
@@ -511,6 +533,8 @@ def time_to_tol(P, precision, problem="c60_128", tol=1e-8, order=12, tau=0.5, n=
     h.close()
     out = {"seconds": dt, "fp32_steps": steps32, "fp64_steps": steps64,
            "max_abs_error_ha": err, "reached": err < tol, "launch_shapes": tuned}
+    if fp64_eval:
+        out["fp64_evaluations"] = evals
     if per_state and E is not None:
         out["errors_ha"] = [float(f"{x:.3e}") for x in (E[:n] - E_ref)]
     return out
@@ -1198,7 +1222,9 @@ def main():
                "reference": f"{c60['eref']} (the oracle's LOBPCG eigenvalues of the grid "
                             "Hamiltonian, certified by residual norms)",
                "tol_ha": 1e-8,
-               "mixed": time_to_tol(P, P.ITP_MIXED, per_state=True, **C60_TTT)}
+               "mixed": time_to_tol(P, P.ITP_MIXED, per_state=True, fp64_eval=True, margin=100.0,
+                                    **C60_TTT),
+               "mixed_fp64_polish_steps": time_to_tol(P, P.ITP_MIXED, **C60_TTT)}
         if args.fp64_ttt:
             ttt["fp64"] = time_to_tol(P, P.ITP_FP64, per_state=True, **C60_TTT)
             ttt["speedup_mixed_vs_fp64"] = ttt["fp64"]["seconds"] / ttt["mixed"]["seconds"]

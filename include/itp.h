@@ -62,6 +62,7 @@ typedef enum {
 
 #define ITP_RITZ 1         /* itp_energies: Ritz values, states rotated onto Ritz vectors */
 #define ITP_RITZ_VALUES 2  /* itp_energies: Ritz values only, states left as they are   */
+#define ITP_EVAL_FP64 8    /* itp_energies, mixed precision: evaluate in FP64 (below)    */
 
 typedef struct itp_grid* itp_handle;
 
@@ -130,8 +131,18 @@ int itp_orthonormalize(itp_handle h);
  *     (Eq. 4 keeps the span), so the rotation only matters when individual
  *     Ritz vectors are read out: iterate with ITP_RITZ_VALUES and finish with
  *     one ITP_RITZ.
+ *   ITP_EVAL_FP64 (with 0, ITP_RITZ or ITP_RITZ_VALUES): the final energy
+ *     evaluation of the mixed path in FP64 -- the FP32 states are rounded up
+ *     to FP64, orthonormalised again in FP64 (Eq. 4: FP64 overlap, Cholesky
+ *     and update; the span does not change) and the energies computed in
+ *     FP64.  No propagation step is taken.  The states stay FP64 until the
+ *     next itp_propagate / itp_step, which continues in FP32.  Converged
+ *     FP32 states carry an FP32 rounding error of ~1e-7 in each component;
+ *     FP64 Ritz values of them are accurate to its square, while FP32 energy
+ *     evaluation is accurate only to ~1e-7 relative.  On ITP_FP64 handles
+ *     the flag changes nothing.
  *   E_host may be NULL.  Synchronises; returns a pending ITP_ERR_NOT_PD /
- *   ITP_ERR_NOCONV. */
+ *   ITP_ERR_NOCONV; ITP_ERR_ARG for unknown flags. */
 int itp_energies(itp_handle h, double* E_host, int flags);
 
 /* One whole step -- itp_propagate(order, tau), itp_orthonormalize,

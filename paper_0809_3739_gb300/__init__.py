@@ -1,7 +1,8 @@
 """GB300-native multi-product imaginary-time propagation (Chin, Janecek,
 Krotscheck): a CUDA library with a C ABI (include/itp.h, libitp.so) and its
 ctypes binding."""
-from .itp import (ITP_FP64, ITP_MIXED, ITP_RITZ, ITP_RITZ_VALUES, ITP_STEP_FP64,  # noqa: F401
+from .itp import (ITP_EVAL_FP64, ITP_FP64, ITP_MIXED, ITP_RITZ, ITP_RITZ_VALUES,  # noqa: F401
+                  ITP_STEP_FP64,
                   itp_autotune, itp_get_tuning, itp_set_tuning,
                   ItpBatch, ItpError, ItpGrid, itp_batch_destroy, itp_batch_problem,
                   itp_batch_step, itp_create_batch, itp_create_grid, itp_destroy,

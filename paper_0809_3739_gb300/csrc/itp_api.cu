@@ -1345,10 +1345,27 @@ int itp_orthonormalize(itp_handle h) {
   return ITP_OK;
 }
 
+// ITP_EVAL_FP64: the mixed path's final evaluation in FP64 -- the FP32
+// states rounded up to FP64, orthonormalised again in FP64 (Eq. 4), after
+// which the energies run on the FP64 lane.  No propagation.
+static int eval_fp64(itp_handle h) {
+  if (h->cur64) return ITP_OK;
+  ITP_TRY(alloc_lane<double>(h, h->f64));
+  ITP_LAUNCH(h, ITP_KERNEL_OTHER, (launch_convert<float, double>(
+                                      h->f32.psi, h->acc, (long long)h->m * h->g.n_points,
+                                      h->st)));
+  ITP_TRY(orthonormalize_lane<double>(h));
+  h->cur64 = true;
+  return ITP_OK;
+}
+
 int itp_energies(itp_handle h, double* E_host, int flags) {
   ITP_TRY(check_ready(h, true));
+  if (flags & ~(ITP_RITZ | ITP_RITZ_VALUES | ITP_EVAL_FP64))
+    return fail(h, ITP_ERR_ARG, "unknown energy flags %d", flags);
   h->have_phi = false;
-  return do_energies(h, E_host, flags);
+  if (flags & ITP_EVAL_FP64) ITP_TRY(eval_fp64(h));
+  return do_energies(h, E_host, flags & ~ITP_EVAL_FP64);
 }
 
 int itp_step(itp_handle h, int order, double tau, int flags, double* E_host) {

@@ -293,12 +293,15 @@ constexpr int kApplyNT = 32;                          // points per tile
 constexpr int kMBytes = 128 * 128 * 4;                // one part of M
 constexpr int kXTileBytes = kApplyNT * 128 * 4;       // one part of an X tile
 
-// Thread L of the CTA owns the group (4 points, 4 states) n4 = L & 7,
-// k4 = L >> 3 of a tile: four 16-byte loads along the point axis (one per
-// state row), held in registers; then a 4x4 register transpose and four
-// 16-byte shared stores (one per point, its 4 states = one core-matrix
-// row).  Loading is split from storing so that the next tile's loads are in
-// flight while the current tile is multiplied and written back.
+// Thread L of the CTA owns points n = n4 + 8q (q < 4) of the tile for the
+// states k = 4 k4 + e (e < 4), n4 = L & 7, k4 = L >> 3: sixteen scalar loads
+// (the 8 lanes of a k4 group read 32 consecutive bytes of a state row per
+// load), held in registers; then, per point, one 16-byte shared store of
+// its 4 states = row n & 7 = n4 of core matrix (n >> 3, k4).  The 8 lanes
+// of a quarter-warp write the 8 rows of one core matrix, so the stores are
+// free of bank conflicts.  Loading is split from storing so that the next
+// tile's loads are in flight while the current tile is multiplied and
+// written back.
 static_assert(kTcThreads == 256, "one (4 points, 4 states) group per thread");
 template <typename TX>
 __device__ __forceinline__ void load_points(const TX* __restrict__ X, int m, long long N,
@@ -306,22 +309,13 @@ __device__ __forceinline__ void load_points(const TX* __restrict__ X, int m, lon
   // X points at the block's first state row; m = its rows
   const int L = threadIdx.x;
   const int n4 = L & 7, k4 = L >> 3;   // k4 in 0..31
-  const long long p = p0 + 4 * n4;
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     const int k = 4 * k4 + e;
+    const TX* src = X + (long long)k * N + p0 + n4;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[e][q] = 0.f;
-    if (k < m) {
-      const TX* src = X + (long long)k * N + p;
-      if (p + 3 < N) {
-        ld4(src, v[e]);
-      } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (p + q < N) v[e][q] = ldf(src + q);
-      }
-    }
+    for (int q = 0; q < 4; ++q)
+      v[e][q] = (k < m && p0 + n4 + 8 * q < N) ? ldf(src + 8 * q) : 0.f;
   }
 }
 __device__ __forceinline__ void store_points(const float (&v)[4][4], uint32_t hi_base,
@@ -330,11 +324,10 @@ __device__ __forceinline__ void store_points(const float (&v)[4][4], uint32_t hi
   const int n4 = L & 7, k4 = L >> 3;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const int n = 4 * n4 + q;
     uint32_t h[4], l[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) split_tf32(v[e][q], h[e], l[e]);
-    const uint32_t off = (uint32_t)(((n >> 3) * 32 + k4) * 128 + (n & 7) * 16);
+    const uint32_t off = (uint32_t)((q * 32 + k4) * 128 + n4 * 16);
     st_shared_v4(hi_base + off, h[0], h[1], h[2], h[3]);
     st_shared_v4(lo_base + off, l[0], l[1], l[2], l[3]);
   }

@@ -21,6 +21,7 @@ ITP_FP64 = 0
 ITP_MIXED = 1
 ITP_RITZ = 1
 ITP_RITZ_VALUES = 2
+ITP_EVAL_FP64 = 8
 ITP_STEP_FP64 = 4
 ITP_TUNE_PENCIL_W, ITP_TUNE_SPLIT, ITP_TUNE_ROW_TB, ITP_TUNE_GRAM = 0, 1, 2, 3
 ITP_TUNING_LEN = 4
@@ -413,10 +414,13 @@ class ItpGrid:
     def propagate_romberg6(self, tau):
         itp_propagate_romberg6(self.h, tau)
 
-    def energies(self, ritz=True):
+    def energies(self, ritz=True, fp64=False):
         """ritz: True (values + rotation), "values" (values only) or False
-        (diagonal expectation values)."""
+        (diagonal expectation values).  fp64: the mixed path's final
+        evaluation in FP64 (ITP_EVAL_FP64)."""
         flags = ITP_RITZ_VALUES if ritz == "values" else (ITP_RITZ if ritz else 0)
+        if fp64:
+            flags |= ITP_EVAL_FP64
         out = np.empty(self.m, dtype=np.float64)
         return itp_energies(self.h, out, flags)
 

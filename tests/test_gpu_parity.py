@@ -249,3 +249,25 @@ def test_mixed_dense_steps_at_full_state_count():
     assert _relerr(got[:4], want) < 1e-4
     E_ref, _, _ = O.energies(got, V, g, ritz=True)
     assert np.max(np.abs(E - E_ref)) < 1e-5 * np.max(np.abs(E_ref))
+
+
+def test_fp64_evaluation_of_fp32_states_matches_oracle():
+    """ITP_EVAL_FP64 on a mixed handle: the FP32 states, rounded up to FP64,
+    orthonormalised again in FP64 and their Ritz values taken in FP64, equal
+    the oracle's orthonormalisation and Ritz values of the same FP32 values
+    to FP64 accuracy."""
+    g = GRIDS[1]
+    V = wells_problem(g)
+    m = 6
+    psi = seeded_states(g, m)
+    with _grid_handle(g, m, "mixed", V, psi) as h:
+        h.step(6, 0.3, ritz="values")
+        psi32 = h.get_states()            # the FP32 states, as FP64 values
+        E = h.energies("values", fp64=True)
+        got = h.get_states()
+        E2 = h.step(6, 0.3, ritz="values")   # FP32 steps continue
+    want, _ = O.cholesky_orthonormalize(psi32, g.dV)
+    E_ref, _, _ = O.energies(want, V, g, ritz=True)
+    assert np.max(np.abs(E - E_ref)) < 1e-12 * np.max(np.abs(E_ref))
+    assert _relerr(got, want) < 1e-11   # the states are FP64 after the evaluation
+    assert np.all(np.isfinite(E2))
