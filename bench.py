@@ -83,14 +83,16 @@ def make_inputs(w, rank=0):
 NCU_TRAFFIC = {
     # DRAM bytes (read + write) per full launch from one ncu capture of the
     # 16-state case, scaled by the number of states; valid only while the
-    # kernel's source file is the one that was profiled
+    # kernel's source file is the one that was profiled (the captures were
+    # taken before the passes moved into a header of their own, with the
+    # same kernel code)
     ("c60_128", "plane_merged"): {"bytes": 1.791e9,
-                                  "source": "paper_0809_3739_gb300/csrc/fft_passes.cu",
-                                  "sha1": "3663773ba8b725bbf787510fb6e3647e00cbbbdf",
+                                  "source": "paper_0809_3739_gb300/csrc/fft_passes.cuh",
+                                  "sha1": "45c108a72460d4ffa0d8dfd74337bb4abb548216",
                                   "profile": "profiles/plane_merged_c60_128.md"},
-    ("c60_128", "pencil"): {"bytes": 1.718e9,
-                            "source": "paper_0809_3739_gb300/csrc/fft_passes.cu",
-                            "sha1": "4b63d6767e836d25c60d7178d2f84d0b67ddf33e",
+    ("c60_128", "pencil"): {"bytes": 1.721e9,
+                            "source": "paper_0809_3739_gb300/csrc/fft_passes.cuh",
+                            "sha1": "45c108a72460d4ffa0d8dfd74337bb4abb548216",
                             "profile": "profiles/pencil_c60_128.md"},
 }
 
@@ -931,6 +933,9 @@ def main():
     ap.add_argument("--no-fp64-ttt", dest="fp64_ttt", action="store_false",
                     help="estimate the FP64 path's time to tolerance on the C60-like workload "
                          "from its step time instead of running it (about two minutes)")
+    ap.add_argument("--ttt-orders", action="store_true",
+                    help="also the C60-like time to tolerance (mixed, FP64 evaluation) at orders "
+                         "4-12 and tau 0.5-1.5 (about seven minutes)")
     ap.add_argument("--adaptive-fp64", action="store_true",
                     help="also time the FP64 adaptive iteration (about two minutes)")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
@@ -1232,6 +1237,17 @@ def main():
             # one FP64 step measured; the FP64 path needs at least as many
             # steps as the mixed path took in all (same iteration, FP64 states)
             ttt["fp64"] = fp64_step_extrapolation(P, ttt["mixed"], **C60_TTT)
+        if args.ttt_orders:
+            # the fixed point of the iteration carries the propagator's time-step
+            # error: which orders reach 1e-8 Ha at which tau, and how fast
+            sweep_ttt = {}
+            for o in (4, 6, 8, 12):
+                for t in (0.5, 1.0, 1.5):
+                    cfg = dict(C60_TTT, order=o, tau=t, max_fp64=0)
+                    r = time_to_tol(P, P.ITP_MIXED, fp64_eval=True, margin=100.0, **cfg)
+                    r.pop("launch_shapes", None)
+                    sweep_ttt[f"order{o}_tau{t}"] = r
+            ttt["by_order_and_tau"] = sweep_ttt
         # the 3D oscillator (exact closed-shell energies) with 8 guard states
         ttt_osc = {"workload": f"{TTT_PROBLEMS['osc_128']['desc']}, n = 120 + 8 guard, "
                                "order 12, tau = 0.5, seeded random-normal start",

@@ -28,6 +28,7 @@
 // Kernels are specialised at compile time for the common edge lengths
 // (all index arithmetic folds to constants); a generic instantiation takes
 // the sizes at run time.
+#pragma once
 #include <cooperative_groups.h>
 
 #include "fft_common.cuh"
@@ -181,7 +182,7 @@ struct PlaneGeo {
   // accesses then need no address arithmetic per element.
   static constexpr int XR1 = NX ? AxisT<NX>::R1_ : 0;
   static constexpr int YR1 = NY ? AxisT<NY>::R1_ : 0;
-  static constexpr bool kRowFast = XR1 > 0 && 16 % XR1 == 0;
+  static constexpr bool kRowFast = XR1 > 0 && 16 % (XR1 > 0 ? XR1 : 1) == 0;
   static constexpr bool kColFast = YR1 > 0 && YR1 % 2 == 0;
   __device__ __forceinline__ int rowA(int t, int n1, int j) const {
     if constexpr (kRowFast) return (t * pp + n1) + (XR1 * j + ((XR1 * j) >> 4));
@@ -1492,15 +1493,6 @@ cudaError_t pencil_dispatch(const GridDesc& g, const PencilArgs<R>& a, size_t sm
 
 }  // namespace
 
-int plane_row_pitch(int nx) { return row_pitch(nx); }
-
-size_t plane_smem_bytes(const GridDesc& g, int real_bytes) {
-  return ((size_t)(g.ny / 2) * g.pp + g.nx + g.ny) * 2 * real_bytes;
-}
-size_t pencil_smem_bytes(const GridDesc& g, int real_bytes) {
-  return ((size_t)g.nz * g.pencil_w + g.nz) * 2 * real_bytes;
-}
-
 template <typename R, int NX, int TB>
 cudaError_t rowpass_dispatch(const GridDesc& g, const PlaneArgs<R>& a, cudaStream_t st) {
   const size_t smem = ((size_t)TB * g.pp + g.nx) * 2 * sizeof(R);
@@ -1655,15 +1647,6 @@ cudaError_t launch_plane(const GridDesc& g, const PlaneArgs<R>& a, cudaStream_t 
   return plane_dispatch<R, 0, 0>(g, a, smem, st);
 }
 
-cudaError_t launch_term_sum(const TermSumArgs& a, cudaStream_t st) {
-  if (a.k < 1 || a.k > kMaxTermsK || (a.plane_pts & 3) || (a.plane_pitch & 3))
-    return cudaErrorInvalidValue;
-  const int nvec = a.plane_pts / 4;
-  dim3 grid((nvec + 255) / 256 < 8 ? (nvec + 255) / 256 : 8, (unsigned)((long long)a.m * a.nz));
-  term_sum_kernel<<<grid, 256, 0, st>>>(a);
-  return cudaGetLastError();
-}
-
 template <typename R>
 cudaError_t launch_pencil(const GridDesc& g, const PencilArgs<R>& a, cudaStream_t st) {
   const size_t smem = pencil_smem_bytes(g, sizeof(R));
@@ -1706,28 +1689,5 @@ cudaError_t launch_transpose_planes(const TS* src, TD* dst, long long nplanes, i
   transpose_planes_kernel<TS, TD><<<grid, block, 0, st>>>(src, dst, nplanes, rows, cols);
   return cudaGetLastError();
 }
-
-template cudaError_t launch_plane<float>(const GridDesc&, const PlaneArgs<float>&, cudaStream_t,
-                                         int*);
-template cudaError_t launch_plane<double>(const GridDesc&, const PlaneArgs<double>&, cudaStream_t,
-                                          int*);
-template cudaError_t launch_pencil<float>(const GridDesc&, const PencilArgs<float>&, cudaStream_t);
-template cudaError_t launch_pencil<double>(const GridDesc&, const PencilArgs<double>&, cudaStream_t);
-template cudaError_t launch_term_tables<float>(const GridDesc&, const double*, double, double,
-                                               double, double, float*, float*, float*, float*,
-                                               float*, cudaStream_t);
-template cudaError_t launch_term_tables<double>(const GridDesc&, const double*, double, double,
-                                                double, double, double*, double*, double*,
-                                                double*, double*, cudaStream_t);
-template cudaError_t launch_kinetic_tables<float>(const GridDesc&, double, double, double, float*,
-                                                  float*, float*, cudaStream_t);
-template cudaError_t launch_kinetic_tables<double>(const GridDesc&, double, double, double,
-                                                   double*, double*, double*, cudaStream_t);
-template cudaError_t launch_transpose_planes<double, double>(const double*, double*, long long,
-                                                             int, int, cudaStream_t);
-template cudaError_t launch_transpose_planes<double, float>(const double*, float*, long long, int,
-                                                            int, cudaStream_t);
-template cudaError_t launch_transpose_planes<float, double>(const float*, double*, long long, int,
-                                                            int, cudaStream_t);
 
 }  // namespace itp

@@ -1,5 +1,5 @@
 // Internal launch interface between the C-ABI layer (itp_api.cu) and the
-// device kernels (fft_passes.cu, dense.cu).  Not part of the public ABI.
+// device kernels (fft_passes.cuh, dense.cu, tc_gemm.cu).  Not part of the public ABI.
 #pragma once
 #include <cuda_runtime.h>
 #include <stddef.h>
