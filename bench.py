@@ -854,21 +854,36 @@ def batch_throughput(P, torch, steps, warmup, count=64, order=8, tau=0.25, seed=
         q.synchronize()
         del x
     m_total = b.m_total
-    for q in b.problems:   # launch shapes per problem (untimed)
-        q.autotune(order, tau)
-    for _ in range(warmup):
-        b.step(order, tau)
-    n0 = b.kernel_launches
-    torch.cuda.synchronize()
-    start = torch.cuda.Event(enable_timing=True)
-    end = torch.cuda.Event(enable_timing=True)
-    start.record(stream)
-    for _ in range(steps):
-        E = b.step(order, tau)
-    end.record(stream)
-    end.synchronize()
-    dt = start.elapsed_time(end) / 1e3
-    per_step = (b.kernel_launches - n0) // steps
+    # launch shapes (untimed): tuned on one problem per grid and shared by the
+    # others of that grid, so that they form one group of grouped launches
+    tuned_by_grid = {}
+    for q, (g, _, _) in zip(b.problems, probs):
+        key = (g.nx, g.ny, g.nz)
+        if key not in tuned_by_grid:
+            tuned_by_grid[key], _ = q.autotune(order, tau)
+        else:
+            t = tuned_by_grid[key]
+            q.set_tuning(t["pencil_w"], t["split"], t["row_tb"], t["gram_ctas"])
+
+    def timed(grouped):
+        b.set_grouping(grouped)
+        for _ in range(warmup):
+            b.step(order, tau)
+        n0 = b.kernel_launches
+        torch.cuda.synchronize()
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for _ in range(steps):
+            E = b.step(order, tau)
+        end.record(stream)
+        end.synchronize()
+        return start.elapsed_time(end) / 1e3, (b.kernel_launches - n0) // steps, E
+
+    # one graph branch of ~50 launches per problem, then grouped launches
+    dt_br, per_step_br, _ = timed(False)
+    dt, per_step, E = timed(True)
+    n_groups = b.groups
     # the same problems one after another (each its own step graph)
     for q in b.problems:
         q.step_graph(order, tau)
@@ -888,11 +903,18 @@ def batch_throughput(P, torch, steps, warmup, count=64, order=8, tau=0.25, seed=
     step_b = sum(step_bytes(g, n, order // 2) for g, _, n in probs)
     return {"workload": f"{count} independent random-well problems (seed {seed}+p), grids "
                         f"{sizes}, n = 8..64 states each ({m_total} in all), order 8, "
-                        f"tau = {tau}, mixed precision",
+                        f"tau = {tau}, mixed precision, grouped launches",
             "value": m_total * steps / dt, "unit": "state-steps/s",
             "ms_per_step": 1e3 * dt / steps, "steps": steps,
             "state_points": int(sum(n * g.n_points for g, _, n in probs)),
             "gpu_launches_per_step": per_step, "graph_launches_per_step": 1,
+            "grouped": {"groups": n_groups,
+                        "how": "each FFT pass of the problems that share a grid is one launch "
+                               "over all their states (itp_batch_set_grouping); the n x n "
+                               "kernels run as per-problem branches between those launches"},
+            "branches": {"value": m_total * steps / dt_br, "ms_per_step": 1e3 * dt_br / steps,
+                         "gpu_launches_per_step": per_step_br,
+                         "how": "one graph branch per problem (itp_batch_set_grouping(b, 0))"},
             "roofline": {"bound": "hbm", "algorithmic_bytes_per_step": step_b,
                          "achieved": step_b / (dt / steps) / 1e9, "peak": hbm_peak,
                          "unit": "GB/s", "frac": step_b / (dt / steps) / 1e9 / hbm_peak,

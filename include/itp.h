@@ -375,6 +375,24 @@ int itp_batch_step(itp_batch_handle b, int order, double tau, int flags, double*
  * replay). */
 long long itp_batch_kernel_launches(itp_batch_handle b);
 
+/* How a batch step's graph is built.  grouped != 0 (the default): problems
+ * with the same grid, precision lane, launch shapes and pass sequence form a
+ * group, and each FFT pass of a step (plane, pencil, exact term sum) is one
+ * launch over all the states of the group's problems -- a CTA row looks up
+ * its (problem, state) and that problem's arguments in tables the batch
+ * keeps in device memory -- while the remaining kernels of each problem
+ * (overlap, Cholesky, update, eigenvalues, copies) run as parallel branches
+ * between those launches; groups run as parallel branches.  Every CTA
+ * computes exactly what the problem's own launch would, so results are the
+ * same bit for bit.  grouped == 0: one branch of ~50 launches per problem.
+ * Takes effect at the next itp_batch_step (which captures a new graph).
+ * Returns ITP_OK or ITP_ERR_ARG (null batch). */
+int itp_batch_set_grouping(itp_batch_handle b, int grouped);
+
+/* Number of groups in the captured grouped graph (0 before the first
+ * grouped step, or in the per-problem form). */
+int itp_batch_groups(itp_batch_handle b);
+
 /* One-line description of the last error on the batch; with b == NULL, why
  * the calling thread's last itp_create_batch failed. */
 const char* itp_batch_last_error(itp_batch_handle b);

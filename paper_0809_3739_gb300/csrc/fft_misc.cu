@@ -24,6 +24,16 @@ cudaError_t launch_term_sum(const TermSumArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_term_sum_group(const TermSumArgs* args, const int2* rows, int nrows, int nz,
+                                  int plane_pts, cudaStream_t st) {
+  if ((plane_pts & 3) || nrows < 1 || nrows > 65535 || nz < 1 || nz > 65535)
+    return cudaErrorInvalidValue;
+  const int nvec = plane_pts / 4;
+  dim3 grid((nvec + 255) / 256 < 8 ? (nvec + 255) / 256 : 8, (unsigned)nrows, (unsigned)nz);
+  term_sum_group_kernel<<<grid, 256, 0, st>>>(args, rows);
+  return cudaGetLastError();
+}
+
 template cudaError_t launch_term_tables<float>(const GridDesc&, const double*, double, double,
                                                double, double, float*, float*, float*, float*,
                                                float*, cudaStream_t);

@@ -741,11 +741,11 @@ struct EpiHpsi {
   }
 };
 
+// One plane pass over plane z of state s (the whole-plane kernels below
+// take z, s from the grid; the grouped kernel from a table of rows).
 template <typename R, int NX, int NY, int MODE>
-__global__ void __launch_bounds__(launch_threads(kThreads),
-                                  min_blocks(plane_smem_ct(NX, NY, sizeof(R)),
-                                             sizeof(R) == 4 ? 3 : 2))
-    plane_kernel(const GridDesc g, const PlaneArgs<R> a) {
+__device__ __forceinline__ void plane_body(const GridDesc& g, const PlaneArgs<R>& a, int z,
+                                           int s) {
   using C = typename CplxOf<R>::type;
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int NTT = kThreads;
@@ -756,7 +756,6 @@ __global__ void __launch_bounds__(launch_threads(kThreads),
   for (int i = threadIdx.x; i < G.nx; i += blockDim.x) twx[i] = static_cast<const C*>(a.twx)[i];
   for (int i = threadIdx.x; i < G.ny; i += blockDim.x) twy[i] = static_cast<const C*>(a.twy)[i];
 
-  const int z = blockIdx.x, s = blockIdx.y;
   const long long plane_pts = (long long)G.nx * G.ny;
   const long long real_off = (long long)s * g.n_points + (long long)z * plane_pts;
   const long long spec_off = ((long long)s * g.nz + z) * (long long)G.ny * G.nxh;
@@ -809,6 +808,27 @@ __global__ void __launch_bounds__(launch_threads(kThreads),
   yA<-1>(G, sm, twy);
   __syncthreads();
   yB_fwd_global(G, sm, static_cast<C*>(a.spec) + spec_off, a.kin);
+}
+
+template <typename R, int NX, int NY, int MODE>
+__global__ void __launch_bounds__(launch_threads(kThreads),
+                                  min_blocks(plane_smem_ct(NX, NY, sizeof(R)),
+                                             sizeof(R) == 4 ? 3 : 2))
+    plane_kernel(const GridDesc g, const PlaneArgs<R> a) {
+  plane_body<R, NX, NY, MODE>(g, a, blockIdx.x, blockIdx.y);
+}
+
+// Grouped plane pass: one launch over the states of several problems with
+// the same grid (a batch of independent problems).  CTA row y of the grid
+// is state rows[y].y of problem rows[y].x, whose arguments are args[rows[y].x].
+template <typename R, int NX, int NY, int MODE>
+__global__ void __launch_bounds__(launch_threads(kThreads),
+                                  min_blocks(plane_smem_ct(NX, NY, sizeof(R)),
+                                             sizeof(R) == 4 ? 3 : 2))
+    plane_group_kernel(const GridDesc g, const PlaneArgs<R>* __restrict__ args,
+                       const int2* __restrict__ rows) {
+  const int2 r = rows[blockIdx.y];
+  plane_body<R, NX, NY, MODE>(g, args[r.x], blockIdx.x, r.y);
 }
 
 // ----------------------------------------------------------------------------
@@ -1326,10 +1346,8 @@ __global__ void __launch_bounds__(launch_threads(task_threads(W)))
 // ----------------------------------------------------------------------------
 // Pencil pass.  Slab element (z, column t) at shared position z * W + t.
 template <typename R, int NZ, int W, int MODE>
-__global__ void __launch_bounds__(launch_threads(task_threads(W)),
-                                  min_blocks(pencil_smem_ct(NZ, W, sizeof(R)),
-                                             sizeof(R) == 4 ? 3 : 2))
-    pencil_kernel(const GridDesc g, const PencilArgs<R> a) {
+__device__ __forceinline__ void pencil_body(const GridDesc& g, const PencilArgs<R>& a, int bx,
+                                            int s) {
   constexpr int NT = task_threads(W);
   using C = typename CplxOf<R>::type;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -1339,8 +1357,7 @@ __global__ void __launch_bounds__(launch_threads(task_threads(W)),
   const int pw = W ? W : g.pencil_w;        // slab pitch = block width
   C* twz = sm + nz * pw;
   for (int i = threadIdx.x; i < nz; i += blockDim.x) twz[i] = static_cast<const C*>(a.twz)[i];
-  const int s = blockIdx.y;
-  const int ky = blockIdx.x % g.ny, chunk = blockIdx.x / g.ny;
+  const int ky = bx % g.ny, chunk = bx / g.ny;
   const int kx0 = chunk * pw;
   const int w = min(pw, g.nxh - kx0);
   const long long zstride = (long long)g.ny * g.nxh;
@@ -1354,6 +1371,25 @@ __global__ void __launch_bounds__(launch_threads(task_threads(W)),
                  pw, az.r2, kx0, mode_tag<MODE>())
   __syncthreads();
   ITP_WITH_RADIX(az.r2, pencil_invA_r, nt_tag<NT>(), sm, base, zstride, w, pw, az.r1)
+}
+
+template <typename R, int NZ, int W, int MODE>
+__global__ void __launch_bounds__(launch_threads(task_threads(W)),
+                                  min_blocks(pencil_smem_ct(NZ, W, sizeof(R)),
+                                             sizeof(R) == 4 ? 3 : 2))
+    pencil_kernel(const GridDesc g, const PencilArgs<R> a) {
+  pencil_body<R, NZ, W, MODE>(g, a, blockIdx.x, blockIdx.y);
+}
+
+// Grouped pencil pass (see plane_group_kernel).
+template <typename R, int NZ, int W, int MODE>
+__global__ void __launch_bounds__(launch_threads(task_threads(W)),
+                                  min_blocks(pencil_smem_ct(NZ, W, sizeof(R)),
+                                             sizeof(R) == 4 ? 3 : 2))
+    pencil_group_kernel(const GridDesc g, const PencilArgs<R>* __restrict__ args,
+                        const int2* __restrict__ rows) {
+  const int2 r = rows[blockIdx.y];
+  pencil_body<R, NZ, W, MODE>(g, args[r.x], blockIdx.x, r.y);
 }
 
 // ----------------------------------------------------------------------------
@@ -1398,9 +1434,8 @@ __global__ void term_tables_kernel(const GridDesc g, const double* __restrict__ 
 // FP32 rate, and a plain FP64 sum with its conversions costs an order of
 // magnitude more.
 
-__global__ void term_sum_kernel(const TermSumArgs a) {
-  // blockIdx.y = plane (state, z); x-blocks stride over the plane's float4s
-  const long long pl = blockIdx.y;
+__device__ __forceinline__ void term_sum_body(const TermSumArgs& a, long long pl) {
+  // pl = plane (state, z); x-blocks stride over the plane's float4s
   const int nvec = a.plane_pts >> 2;
   const float4* src[kMaxTermsK];
 #pragma unroll
@@ -1421,6 +1456,17 @@ __global__ void term_sum_kernel(const TermSumArgs a) {
     }
     dst[v] = make_float4(s[0] + e[0], s[1] + e[1], s[2] + e[2], s[3] + e[3]);
   }
+}
+
+__global__ void term_sum_kernel(const TermSumArgs a) { term_sum_body(a, blockIdx.y); }
+
+// Grouped term sum: row y is state rows[y].y of problem rows[y].x, z-plane
+// blockIdx.z.
+__global__ void term_sum_group_kernel(const TermSumArgs* __restrict__ args,
+                                      const int2* __restrict__ rows) {
+  const int2 r = rows[blockIdx.y];
+  const TermSumArgs& a = args[r.x];
+  term_sum_body(a, (long long)r.y * a.nz + blockIdx.z);
 }
 
 // dst[p][c][r] = src[p][r][c] for nplanes planes of rows x cols.
@@ -1688,6 +1734,85 @@ cudaError_t launch_transpose_planes(const TS* src, TD* dst, long long nplanes, i
   dim3 grid((cols + 31) / 32, (rows + 31) / 32, (unsigned)nplanes);
   transpose_planes_kernel<TS, TD><<<grid, block, 0, st>>>(src, dst, nplanes, rows, cols);
   return cudaGetLastError();
+}
+
+// ---- grouped launches (batches of problems with the same grid) -------------
+template <typename R, int NX, int NY>
+cudaError_t plane_group_dispatch(const GridDesc& g, int mode, const PlaneArgs<R>* args,
+                                 const int2* rows, int nrows, size_t smem, cudaStream_t st) {
+  dim3 grid(g.nz, nrows);
+  cudaError_t e;
+  switch (mode) {
+#define ITP_PLANE_GROUP_CASE(M)                                             \
+  case M:                                                                   \
+    e = set_smem(plane_group_kernel<R, NX, NY, M>, smem);                   \
+    if (e != cudaSuccess) return e;                                         \
+    plane_group_kernel<R, NX, NY, M><<<grid, kThreads, smem, st>>>(g, args, rows); \
+    break;
+    ITP_PLANE_GROUP_CASE(PLANE_FWD_REAL)
+    ITP_PLANE_GROUP_CASE(PLANE_MERGED)
+    ITP_PLANE_GROUP_CASE(PLANE_COMBINE)
+    ITP_PLANE_GROUP_CASE(PLANE_HPSI)
+    ITP_PLANE_GROUP_CASE(PLANE_TERM)
+#undef ITP_PLANE_GROUP_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_plane_group(const GridDesc& g, int mode, const PlaneArgs<R>* args,
+                               const int2* rows, int nrows, cudaStream_t st) {
+  if (g.split_planes[sizeof(R) == 4 ? 0 : 1]) return cudaErrorInvalidValue;   // whole planes only
+  const size_t smem = plane_smem_bytes(g, sizeof(R));
+  if (g.nx == g.ny && g.pp == row_pitch(g.nx)) {
+    switch (g.nx) {
+      case 32: return plane_group_dispatch<R, 32, 32>(g, mode, args, rows, nrows, smem, st);
+      case 48: return plane_group_dispatch<R, 48, 48>(g, mode, args, rows, nrows, smem, st);
+      case 64: return plane_group_dispatch<R, 64, 64>(g, mode, args, rows, nrows, smem, st);
+      case 96: return plane_group_dispatch<R, 96, 96>(g, mode, args, rows, nrows, smem, st);
+      case 128: return plane_group_dispatch<R, 128, 128>(g, mode, args, rows, nrows, smem, st);
+      default: break;
+    }
+  }
+  return plane_group_dispatch<R, 0, 0>(g, mode, args, rows, nrows, smem, st);
+}
+
+template <typename R, int NZ, int W>
+cudaError_t pencil_group_dispatch(const GridDesc& g, int mode, const PencilArgs<R>* args,
+                                  const int2* rows, int nrows, size_t smem, cudaStream_t st) {
+  const int chunks = (g.nxh + g.pencil_w - 1) / g.pencil_w;
+  dim3 grid(g.ny * chunks, nrows);
+  const int nthr = launch_threads(task_threads(W));
+  cudaError_t e;
+  if (mode == PENCIL_PROPAGATE) {
+    e = set_smem(pencil_group_kernel<R, NZ, W, PENCIL_PROPAGATE>, smem);
+    if (e != cudaSuccess) return e;
+    pencil_group_kernel<R, NZ, W, PENCIL_PROPAGATE><<<grid, nthr, smem, st>>>(g, args, rows);
+  } else {
+    e = set_smem(pencil_group_kernel<R, NZ, W, PENCIL_KINETIC>, smem);
+    if (e != cudaSuccess) return e;
+    pencil_group_kernel<R, NZ, W, PENCIL_KINETIC><<<grid, nthr, smem, st>>>(g, args, rows);
+  }
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_pencil_group(const GridDesc& g, int mode, const PencilArgs<R>* args,
+                                const int2* rows, int nrows, cudaStream_t st) {
+  const size_t smem = pencil_smem_bytes(g, sizeof(R));
+  switch (g.nz * 1000 + g.pencil_w) {
+    case 32 * 1000 + 17: return pencil_group_dispatch<R, 32, 17>(g, mode, args, rows, nrows, smem, st);
+    case 48 * 1000 + 25: return pencil_group_dispatch<R, 48, 25>(g, mode, args, rows, nrows, smem, st);
+    case 64 * 1000 + 33: return pencil_group_dispatch<R, 64, 33>(g, mode, args, rows, nrows, smem, st);
+    case 96 * 1000 + 49: return pencil_group_dispatch<R, 96, 49>(g, mode, args, rows, nrows, smem, st);
+    case 96 * 1000 + 25: return pencil_group_dispatch<R, 96, 25>(g, mode, args, rows, nrows, smem, st);
+    case 128 * 1000 + 65: return pencil_group_dispatch<R, 128, 65>(g, mode, args, rows, nrows, smem, st);
+    case 128 * 1000 + 33: return pencil_group_dispatch<R, 128, 33>(g, mode, args, rows, nrows, smem, st);
+    default: break;
+  }
+  return pencil_group_dispatch<R, 0, 0>(g, mode, args, rows, nrows, smem, st);
 }
 
 }  // namespace itp

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <string>
 #include <vector>
@@ -45,6 +46,23 @@ struct Lane {
   double tab_tau = 0.0;
 };
 
+// One recorded kernel launch of a problem's step (batches, itp_batch_step):
+// the FFT passes keep their arguments, so that the same pass of several
+// problems with one grid can run as one grouped launch; every other launch
+// keeps a closure that issues it on the problem's stream.
+struct RecOp {
+  enum Kind { kOther = 0, kPlane = 1, kPencil = 2, kTermSum = 3 };
+  int kind = kOther;
+  int lane = 0;               // 0: FP32 arguments, 1: FP64
+  int mode = 0;               // plane or pencil mode
+  PlaneArgs<float> p32{};
+  PlaneArgs<double> p64{};
+  PencilArgs<float> e32{};
+  PencilArgs<double> e64{};
+  TermSumArgs ts{};
+  std::function<cudaError_t()> fn;   // the launch on the problem's stream
+};
+
 }  // namespace
 
 struct itp_grid {
@@ -75,6 +93,7 @@ struct itp_grid {
   double* res_dev = nullptr;  // [2m] residual norms of the adaptive iteration
   long long launches = 0;
   int expire_waits = 0;       // test hook: tensor-core launches left that expire their wait
+  std::vector<RecOp>* rec = nullptr;   // recording a step instead of launching it
   std::string err;
   bool own_stream = false;    // created by the library (no stream given)
   // CUDA graph of one step (itp_step): propagate + orthonormalize + energies
@@ -121,11 +140,31 @@ int fail(itp_handle h, int code, const char* fmt, ...) {
   } while (0)
 
 // Launch one kernel of the given ITP_KERNEL_* kind, counted and (when
-// profiling is on) bracketed by CUDA events on the handle's stream.
+// profiling is on) bracketed by CUDA events on the handle's stream.  While
+// the handle records a step (h->rec), the launch is kept as a closure to be
+// issued later on the handle's stream instead.
 #define ITP_LAUNCH(h, kind, expr)                                                         \
   do {                                                                                    \
     (h)->launches++;                                                                      \
+    if ((h)->rec) {                                                                       \
+      RecOp op_;                                                                          \
+      op_.fn = [=]() -> cudaError_t { return (expr); };                                   \
+      (h)->rec->push_back(std::move(op_));                                                \
+      break;                                                                              \
+    }                                                                                     \
     const long ev_ = prof_begin(h, kind);                                                 \
+    cudaError_t e_ = (expr);                                                              \
+    prof_end(h, ev_);                                                                     \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(h, ITP_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_));              \
+  } while (0)
+
+// The same for an FFT pass: while recording, the pass function itself keeps
+// its arguments (plane_counted, pencil_counted, term_sum_counted).
+#define ITP_LAUNCH_PASS(h, kind, expr)                                                    \
+  do {                                                                                    \
+    (h)->launches++;                                                                      \
+    const long ev_ = (h)->rec ? -1 : prof_begin(h, kind);                                 \
     cudaError_t e_ = (expr);                                                              \
     prof_end(h, ev_);                                                                     \
     if (e_ != cudaSuccess)                                                                \
@@ -295,10 +334,49 @@ void free_lane(Lane<R>& L) {
 // A plane pass: 1 kernel, or 2-3 kernels on split planes (counted).
 template <typename R>
 cudaError_t plane_counted(itp_handle h, const PlaneArgs<R>& a) {
+  if (h->rec) {
+    RecOp op;
+    op.kind = RecOp::kPlane;
+    op.lane = sizeof(R) == 8;
+    op.mode = a.mode;
+    if constexpr (sizeof(R) == 4) op.p32 = a;
+    else op.p64 = a;
+    op.fn = [h, a]() { int n = 1; return launch_plane<R>(h->g, a, h->st, &n); };
+    h->rec->push_back(std::move(op));
+    return cudaSuccess;
+  }
   int n = 1;
   const cudaError_t e = launch_plane<R>(h->g, a, h->st, &n);
   h->launches += n - 1;
   return e;
+}
+
+template <typename R>
+cudaError_t pencil_counted(itp_handle h, const PencilArgs<R>& a) {
+  if (h->rec) {
+    RecOp op;
+    op.kind = RecOp::kPencil;
+    op.lane = sizeof(R) == 8;
+    op.mode = a.mode;
+    if constexpr (sizeof(R) == 4) op.e32 = a;
+    else op.e64 = a;
+    op.fn = [h, a]() { return launch_pencil<R>(h->g, a, h->st); };
+    h->rec->push_back(std::move(op));
+    return cudaSuccess;
+  }
+  return launch_pencil<R>(h->g, a, h->st);
+}
+
+cudaError_t term_sum_counted(itp_handle h, const TermSumArgs& a) {
+  if (h->rec) {
+    RecOp op;
+    op.kind = RecOp::kTermSum;
+    op.ts = a;
+    op.fn = [h, a]() { return launch_term_sum(a, h->st); };
+    h->rec->push_back(std::move(op));
+    return cudaSuccess;
+  }
+  return launch_term_sum(a, h->st);
 }
 
 template <typename R>
@@ -374,7 +452,7 @@ int propagate_lane(itp_handle h, int k, double tau, int s0 = 0, const R* in = nu
       pa.kin.fz = kt + g.nxh + g.ny;
       pa.kin.mode = 0;
     }
-    ITP_LAUNCH(h, ITP_KERNEL_PLANE_FWD, plane_counted<R>(h, pa));
+    ITP_LAUNCH_PASS(h, ITP_KERNEL_PLANE_FWD, plane_counted<R>(h, pa));
     PencilArgs<R> pe{};
     pe.mode = PENCIL_PROPAGATE;
     pe.m = ms;
@@ -386,14 +464,15 @@ int propagate_lane(itp_handle h, int k, double tau, int s0 = 0, const R* in = nu
     pe.twz = L.twz;
     for (int j = 1; j <= i; ++j) {
       if (!planar)
-        ITP_LAUNCH(h, pe.mode == PENCIL_PROPAGATE ? ITP_KERNEL_PENCIL : ITP_KERNEL_PENCIL_KINETIC,
-                   launch_pencil<R>(g, pe, h->st));
+        ITP_LAUNCH_PASS(h, pe.mode == PENCIL_PROPAGATE ? ITP_KERNEL_PENCIL
+                                                       : ITP_KERNEL_PENCIL_KINETIC,
+                        pencil_counted<R>(h, pe));
       if (j < i) {
         PlaneArgs<R> pm = pa;
         pm.mode = PLANE_MERGED;
         pm.f_in = nullptr;
         pm.f_mid = L.f_full[i - 1];
-        ITP_LAUNCH(h, ITP_KERNEL_PLANE_MERGED, plane_counted<R>(h, pm));
+        ITP_LAUNCH_PASS(h, ITP_KERNEL_PLANE_MERGED, plane_counted<R>(h, pm));
       }
     }
     if (fused) {
@@ -403,7 +482,7 @@ int propagate_lane(itp_handle h, int k, double tau, int s0 = 0, const R* in = nu
       pt.f_in = nullptr;
       pt.f_out = L.f_half[i - 1];
       pt.coef = mp_coefficient(i, k);
-      ITP_LAUNCH(h, ITP_KERNEL_PLANE_COMBINE, plane_counted<R>(h, pt));
+      ITP_LAUNCH_PASS(h, ITP_KERNEL_PLANE_COMBINE, plane_counted<R>(h, pt));
       ts.term[i - 1] = reinterpret_cast<const float*>(work);
       continue;
     }
@@ -416,7 +495,7 @@ int propagate_lane(itp_handle h, int k, double tau, int s0 = 0, const R* in = nu
     pc.acc_init = (i == 1);
     // the mixed path keeps the sum in FP64 and rounds the finished phi once
     pc.phi_out = (sizeof(R) == 4 && i == k) ? (out ? out : L.psi_tmp) + so * g.n_points : nullptr;
-    ITP_LAUNCH(h, ITP_KERNEL_PLANE_COMBINE, plane_counted<R>(h, pc));
+    ITP_LAUNCH_PASS(h, ITP_KERNEL_PLANE_COMBINE, plane_counted<R>(h, pc));
   }
   if (fused) {
     // phi = sum_i c_i f u_i in FP64 over the FP32 contributions
@@ -426,7 +505,7 @@ int propagate_lane(itp_handle h, int k, double tau, int s0 = 0, const R* in = nu
     ts.plane_pts = g.nx * g.ny;
     ts.plane_pitch = 2LL * g.ny * g.nxh;
     ts.phi_out = reinterpret_cast<float*>((out ? out : L.psi_tmp) + so * g.n_points);
-    ITP_LAUNCH(h, ITP_KERNEL_OTHER, launch_term_sum(ts, h->st));
+    ITP_LAUNCH_PASS(h, ITP_KERNEL_OTHER, term_sum_counted(h, ts));
   }
   return ITP_OK;
 }
@@ -489,7 +568,7 @@ int energies_lane(itp_handle h, int flags) {
     pa.kin.mode = 1;
     pa.kin.scale = (R)(1.0 / (double)g.n_points);
   }
-  ITP_LAUNCH(h, ITP_KERNEL_PLANE_FWD, plane_counted<R>(h, pa));
+  ITP_LAUNCH_PASS(h, ITP_KERNEL_PLANE_FWD, plane_counted<R>(h, pa));
   pa.kin = KinFac<R>{};
   PencilArgs<R> pe{};
   pe.mode = PENCIL_KINETIC;
@@ -501,8 +580,8 @@ int energies_lane(itp_handle h, int flags) {
   pe.scale = (R)(1.0 / (double)g.n_points);
   pe.twz = L.twz;
   if (!planar)
-    ITP_LAUNCH(h, pe.mode == PENCIL_PROPAGATE ? ITP_KERNEL_PENCIL : ITP_KERNEL_PENCIL_KINETIC,
-               launch_pencil<R>(g, pe, h->st));
+    ITP_LAUNCH_PASS(h, pe.mode == PENCIL_PROPAGATE ? ITP_KERNEL_PENCIL : ITP_KERNEL_PENCIL_KINETIC,
+                    pencil_counted<R>(h, pe));
   PlaneArgs<R> ph = pa;
   ph.mode = PLANE_HPSI;
   ph.acc = h->acc;
@@ -511,7 +590,7 @@ int energies_lane(itp_handle h, int flags) {
     ph.V_r = L.Vr;
     ph.phi_out = L.psi_tmp;
   }
-  ITP_LAUNCH(h, ITP_KERNEL_PLANE_HPSI, plane_counted<R>(h, ph));
+  ITP_LAUNCH_PASS(h, ITP_KERNEL_PLANE_HPSI, plane_counted<R>(h, ph));
   if (sizeof(R) == 4) {
     ITP_LAUNCH(h, ITP_KERNEL_GRAM, (launch_tc_gram(
                                        reinterpret_cast<const float*>(L.psi),
@@ -1029,6 +1108,13 @@ struct itp_batch {
   std::vector<int> versions;   // problems' launch-shape versions at capture
   long long step_launches = 0, launches = 0;
   std::string err;
+  // grouped launches (itp_batch_set_grouping): the argument tables of the
+  // captured graph's grouped passes, and the events that fork and join the
+  // per-problem branches between them
+  bool grouped = true;
+  void* tables = nullptr;
+  std::vector<cudaEvent_t> evpool;
+  int n_groups = 0;
 };
 
 namespace {
@@ -1039,6 +1125,248 @@ int batch_fail(itp_batch* b, int code, const std::string& msg) {
   if (b) b->err = msg;
   else g_batch_create_error = msg;
   return code;
+}
+
+// Record one whole step of a problem (the kernels of itp_step, and the
+// copies of its energies and status word) without launching anything.
+template <typename R>
+int record_step(itp_handle h, int k, double tau, int flags, std::vector<RecOp>* ops) {
+  h->rec = ops;
+  int rc = propagate_lane<R>(h, k, tau);
+  if (rc == ITP_OK) rc = orthonormalize_lane<R>(h);
+  if (rc == ITP_OK) rc = energies_lane<R>(h, flags);
+  h->rec = nullptr;
+  if (rc != ITP_OK) return rc;
+  RecOp e, st;
+  e.fn = [h]() {
+    return cudaMemcpyAsync(h->E_host_pinned, h->E_dev, h->m * sizeof(double),
+                           cudaMemcpyDeviceToHost, h->st);
+  };
+  st.fn = [h]() {
+    return cudaMemcpyAsync(h->status_host, h->status, sizeof(int), cudaMemcpyDeviceToHost,
+                           h->st);
+  };
+  ops->push_back(std::move(e));
+  ops->push_back(std::move(st));
+  return ITP_OK;
+}
+
+// A recorded pass that can run as a grouped launch: every FFT pass except
+// plane passes on planes too large for one CTA (row + column passes).
+bool groupable(const RecOp& op, itp_handle h) {
+  return op.kind != RecOp::kOther && !(op.kind == RecOp::kPlane && h->g.split_planes[op.lane]);
+}
+
+// Grid, precision lane and launch shapes of a problem, and the kinds and
+// modes of its recorded passes: problems with equal keys can share grouped
+// launches pass by pass.
+std::string group_key(itp_handle h, const std::vector<RecOp>& ops) {
+  const int lane = h->cur64 ? 1 : 0;
+  std::string key = std::to_string(h->g.nx) + "x" + std::to_string(h->g.ny) + "x" +
+                    std::to_string(h->g.nz) + "|" + std::to_string(lane) + "|" +
+                    std::to_string(h->g.pencil_w) + "|" +
+                    std::to_string(h->g.split_planes[lane]) + "|";
+  for (const RecOp& op : ops) {
+    key += (char)('a' + op.kind);
+    key += (char)('0' + op.mode);
+  }
+  return key;
+}
+
+// Build the graph of one step of every problem with grouped launches: each
+// FFT pass (plane, pencil, exact term sum) of the problems in a group (same
+// grid, lane, launch shapes and pass sequence) is one launch over all their
+// states; the other kernels (overlap, Cholesky, update, eigenvalues, the
+// copies) run between those launches as one branch per problem.  Groups run
+// as parallel branches.  The argument tables are copied to the device
+// before the capture.
+int build_grouped_graph(itp_batch* b, int k, double tau, int eflags, cudaGraph_t* graph_out) {
+  const int np = (int)b->probs.size();
+  std::vector<std::vector<RecOp>> ops(np);
+  for (int p = 0; p < np; ++p) {
+    itp_handle h = b->probs[p];
+    const int rc = h->cur64 ? record_step<double>(h, k, tau, eflags, &ops[p])
+                            : record_step<float>(h, k, tau, eflags, &ops[p]);
+    if (rc != ITP_OK)
+      return batch_fail(b, rc, "problem " + std::to_string(p) + ": " + h->err);
+  }
+  std::vector<std::string> keys(np);
+  std::vector<std::vector<int>> groups;
+  for (int p = 0; p < np; ++p) {
+    keys[p] = group_key(b->probs[p], ops[p]);
+    bool placed = false;
+    for (auto& G : groups)
+      if (keys[G[0]] == keys[p]) {
+        G.push_back(p);
+        placed = true;
+        break;
+      }
+    if (!placed) groups.push_back({p});
+  }
+  // argument tables: per group and grouped pass, the members' arguments and
+  // the (member, state / plane) of every CTA row, 256-byte aligned
+  std::vector<unsigned char> host;
+  auto put = [&host](const void* src, size_t bytes) {
+    const size_t off = (host.size() + 255) & ~(size_t)255;
+    host.resize(off + bytes);
+    memcpy(host.data() + off, src, bytes);
+    return off;
+  };
+  struct Planned { size_t args, rows; int nrows; };
+  std::vector<std::vector<Planned>> plan(groups.size());
+  size_t n_events = 1;
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    const std::vector<int>& G = groups[gi];
+    const std::vector<RecOp>& o0 = ops[G[0]];
+    plan[gi].resize(o0.size(), Planned{0, 0, 0});
+    n_events += 1;
+    for (size_t t = 0; t < o0.size(); ++t) {
+      if (!groupable(o0[t], b->probs[G[0]])) {
+        if (t == 0 || groupable(o0[t - 1], b->probs[G[0]])) n_events += G.size();
+        continue;
+      }
+      if (G.size() < 2) continue;
+      std::vector<int2> rows;
+      std::vector<unsigned char> args;
+      for (int q = 0; q < (int)G.size(); ++q) {
+        const RecOp& op = ops[G[q]][t];
+        int nrow = 0;
+        const void* a = nullptr;
+        size_t asz = 0;
+        if (op.kind == RecOp::kPlane) {
+          nrow = op.lane ? op.p64.m : op.p32.m;
+          a = op.lane ? (const void*)&op.p64 : (const void*)&op.p32;
+          asz = op.lane ? sizeof(op.p64) : sizeof(op.p32);
+        } else if (op.kind == RecOp::kPencil) {
+          nrow = op.lane ? op.e64.m : op.e32.m;
+          a = op.lane ? (const void*)&op.e64 : (const void*)&op.e32;
+          asz = op.lane ? sizeof(op.e64) : sizeof(op.e32);
+        } else {
+          nrow = op.ts.m;
+          a = &op.ts;
+          asz = sizeof(op.ts);
+        }
+        for (int r = 0; r < nrow; ++r) rows.push_back(make_int2(q, r));
+        const size_t o = args.size();
+        args.resize(o + asz);
+        memcpy(args.data() + o, a, asz);
+      }
+      if (rows.size() > 65535)
+        return batch_fail(b, ITP_ERR_ARG, "a group has more than 65535 states; "
+                                          "use itp_batch_set_grouping(b, 0)");
+      Planned pl;
+      pl.args = put(args.data(), args.size());
+      pl.rows = put(rows.data(), rows.size() * sizeof(int2));
+      pl.nrows = (int)rows.size();
+      plan[gi][t] = pl;
+    }
+  }
+  if (b->tables) {
+    cudaFree(b->tables);
+    b->tables = nullptr;
+  }
+  if (!host.empty()) {
+    if (cudaMalloc(&b->tables, host.size()) != cudaSuccess)
+      return batch_fail(b, ITP_ERR_OOM, "grouped argument tables");
+    if (cudaMemcpy(b->tables, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return batch_fail(b, ITP_ERR_CUDA, "grouped argument tables");
+  }
+  while (b->evpool.size() < n_events) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return batch_fail(b, ITP_ERR_CUDA, "events");
+    b->evpool.push_back(e);
+  }
+  unsigned char* dev = static_cast<unsigned char*>(b->tables);
+  size_t ev = 0;
+  auto next_event = [&]() { return b->evpool[ev++]; };
+  if (cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return batch_fail(b, ITP_ERR_CUDA, "begin capture");
+  cudaError_t e = cudaSuccess;
+  cudaEvent_t fork = next_event();
+  e = cudaEventRecord(fork, b->st);
+  for (size_t gi = 0; gi < groups.size() && e == cudaSuccess; ++gi) {
+    const std::vector<int>& G = groups[gi];
+    itp_handle h0 = b->probs[G[0]];
+    cudaStream_t gst = h0->st;
+    e = cudaStreamWaitEvent(gst, fork, 0);
+    const std::vector<RecOp>& o0 = ops[G[0]];
+    for (size_t t = 0; t < o0.size() && e == cudaSuccess;) {
+      if (groupable(o0[t], h0)) {
+        if (G.size() < 2) {
+          e = o0[t].fn();
+        } else {
+          const Planned& pl = plan[gi][t];
+          const int2* rows = reinterpret_cast<const int2*>(dev + pl.rows);
+          const RecOp& op = o0[t];
+          if (op.kind == RecOp::kPlane)
+            e = op.lane ? launch_plane_group<double>(
+                              h0->g, op.mode, reinterpret_cast<const PlaneArgs<double>*>(dev + pl.args),
+                              rows, pl.nrows, gst)
+                        : launch_plane_group<float>(
+                              h0->g, op.mode, reinterpret_cast<const PlaneArgs<float>*>(dev + pl.args),
+                              rows, pl.nrows, gst);
+          else if (op.kind == RecOp::kPencil)
+            e = op.lane ? launch_pencil_group<double>(
+                              h0->g, op.mode, reinterpret_cast<const PencilArgs<double>*>(dev + pl.args),
+                              rows, pl.nrows, gst)
+                        : launch_pencil_group<float>(
+                              h0->g, op.mode, reinterpret_cast<const PencilArgs<float>*>(dev + pl.args),
+                              rows, pl.nrows, gst);
+          else
+            e = launch_term_sum_group(reinterpret_cast<const TermSumArgs*>(dev + pl.args), rows,
+                                      pl.nrows, op.ts.nz, op.ts.plane_pts, gst);
+        }
+        ++t;
+        continue;
+      }
+      // a run of other kernels: one branch per member problem
+      size_t t2 = t;
+      while (t2 < o0.size() && !groupable(o0[t2], h0)) ++t2;
+      cudaEvent_t f = next_event();
+      e = cudaEventRecord(f, gst);
+      for (size_t q = 0; q < G.size() && e == cudaSuccess; ++q) {
+        itp_handle hq = b->probs[G[q]];
+        if (q > 0) e = cudaStreamWaitEvent(hq->st, f, 0);
+        for (size_t u = t; u < t2 && e == cudaSuccess; ++u) e = ops[G[q]][u].fn();
+        if (q > 0 && e == cudaSuccess) {
+          cudaEvent_t j = next_event();
+          e = cudaEventRecord(j, hq->st);
+          if (e == cudaSuccess) e = cudaStreamWaitEvent(gst, j, 0);
+        }
+      }
+      t = t2;
+    }
+    if (e == cudaSuccess) {
+      cudaEvent_t j = next_event();
+      e = cudaEventRecord(j, gst);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->st, j, 0);
+    }
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(b->st, &graph);
+  if (e != cudaSuccess || ec != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return batch_fail(b, ITP_ERR_CUDA, std::string("grouped capture: ") +
+                                           cudaGetErrorString(e != cudaSuccess ? e : ec));
+  }
+  b->n_groups = (int)groups.size();
+  *graph_out = graph;
+  return ITP_OK;
+}
+
+// Kernel nodes of a graph (the launches one replay makes).
+long long graph_kernels(cudaGraph_t graph) {
+  size_t n = 0;
+  if (cudaGraphGetNodes(graph, nullptr, &n) != cudaSuccess || n == 0) return 0;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (cudaGraphGetNodes(graph, nodes.data(), &n) != cudaSuccess) return 0;
+  long long k = 0;
+  for (size_t i = 0; i < n; ++i) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+  }
+  return k;
 }
 
 }  // namespace
@@ -1638,6 +1966,8 @@ void itp_batch_destroy(itp_batch_handle b) {
   if (b->fork) cudaEventDestroy(b->fork);
   for (cudaEvent_t e : b->join)
     if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : b->evpool) cudaEventDestroy(e);
+  cudaFree(b->tables);
   if (b->own_stream) cudaStreamDestroy(b->st);
   delete b;
 }
@@ -1733,6 +2063,33 @@ int itp_batch_step(itp_batch_handle b, int order, double tau, int flags, double*
     }
     if (cudaStreamSynchronize(b->st) != cudaSuccess)
       return batch_fail(b, ITP_ERR_CUDA, "synchronise before capture");
+    if (b->grouped) {
+      std::vector<long long> l0(np);
+      for (int p = 0; p < np; ++p) {
+        l0[p] = b->probs[p]->launches;
+        b->probs[p]->capturing = true;
+      }
+      cudaGraph_t graph = nullptr;
+      const int rcg = build_grouped_graph(b, k, tau, eflags, &graph);
+      for (int p = 0; p < np; ++p) {
+        b->probs[p]->capturing = false;
+        b->probs[p]->launches = l0[p];
+      }
+      if (rcg != ITP_OK) return rcg;
+      const long long nk = graph_kernels(graph);
+      const cudaError_t ei = cudaGraphInstantiate(&b->exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ei != cudaSuccess)
+        return batch_fail(b, ITP_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(ei));
+      b->order = order;
+      b->tau = tau;
+      b->flags = flags;
+      b->step_launches = nk;
+      b->versions.resize(np);
+      for (int p = 0; p < np; ++p) b->versions[p] = b->probs[p]->tune_version;
+    }
+  }
+  if (!b->exec) {
     if (cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       return batch_fail(b, ITP_ERR_CUDA, "begin capture");
     cudaEventRecord(b->fork, b->st);
@@ -1791,9 +2148,9 @@ int itp_batch_step(itp_batch_handle b, int order, double tau, int flags, double*
     if (stw) {
       cudaMemsetAsync(h->status, 0, sizeof(int), h->st);
       int rc = ITP_OK;
-      if (stw & 1) rc = fail(h, ITP_ERR_NOT_PD, "overlap matrix is not positive definite");
+      if (stw & 4) rc = fail(h, ITP_ERR_TIMEOUT, "a bounded tensor-core wait expired");
+      else if (stw & 1) rc = fail(h, ITP_ERR_NOT_PD, "overlap matrix is not positive definite");
       else if (stw & 2) rc = fail(h, ITP_ERR_NOCONV, "eigensolver did not converge");
-      else if (stw & 4) rc = fail(h, ITP_ERR_TIMEOUT, "a bounded tensor-core wait expired");
       if (rc != ITP_OK && first == ITP_OK) first = prob_fail(p, rc);
     }
     if (E_host) memcpy(E_host + b->e_off[p], h->E_host_pinned, h->m * sizeof(double));
@@ -1802,6 +2159,20 @@ int itp_batch_step(itp_batch_handle b, int order, double tau, int flags, double*
 }
 
 long long itp_batch_kernel_launches(itp_batch_handle b) { return b ? b->launches : 0; }
+
+int itp_batch_set_grouping(itp_batch_handle b, int grouped) {
+  if (!b) return ITP_ERR_ARG;
+  if ((grouped != 0) != b->grouped) {
+    b->grouped = grouped != 0;
+    if (b->exec) {   // the next step captures the graph in the new form
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+  }
+  return ITP_OK;
+}
+
+int itp_batch_groups(itp_batch_handle b) { return b && b->exec && b->grouped ? b->n_groups : 0; }
 
 const char* itp_batch_last_error(itp_batch_handle b) {
   return b ? b->err.c_str() : g_batch_create_error.c_str();

@@ -101,6 +101,20 @@ size_t plane_smem_bytes(const GridDesc& g, int real_bytes);
 int plane_row_pitch(int nx);   // odd pitch (complex) of a row pair in shared memory
 size_t pencil_smem_bytes(const GridDesc& g, int real_bytes);
 
+// Grouped launches over several problems with the same grid and launch
+// shapes (batches): args[p] are problem p's arguments (device memory),
+// rows[y] = (problem, state) of CTA row y, nrows (<= 65535) rows in all;
+// the term sum takes the z planes as a third grid dimension.  Whole-plane
+// passes only.
+template <typename R>
+cudaError_t launch_plane_group(const GridDesc& g, int mode, const PlaneArgs<R>* args,
+                               const int2* rows, int nrows, cudaStream_t st);
+template <typename R>
+cudaError_t launch_pencil_group(const GridDesc& g, int mode, const PencilArgs<R>* args,
+                                const int2* rows, int nrows, cudaStream_t st);
+cudaError_t launch_term_sum_group(const TermSumArgs* args, const int2* rows, int nrows, int nz,
+                                  int plane_pts, cudaStream_t st);
+
 // One plane pass (*nlaunch receives the number of kernels: 1, or 2-3 when
 // the planes are split into row and column passes).
 template <typename R>

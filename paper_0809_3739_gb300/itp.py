@@ -70,6 +70,8 @@ SIGNATURES = [
     ("itp_batch_count", _I, [_H]),
     ("itp_batch_step", _I, [_H, _I, _D, _I, _PD]),
     ("itp_batch_kernel_launches", ctypes.c_longlong, [_H]),
+    ("itp_batch_set_grouping", _I, [_H, _I]),
+    ("itp_batch_groups", _I, [_H]),
     ("itp_batch_last_error", ctypes.c_char_p, [_H]),
     ("itp_batch_destroy", None, [_H]),
 ]
@@ -515,6 +517,15 @@ class ItpBatch:
     @property
     def kernel_launches(self):
         return int(load().itp_batch_kernel_launches(self.b))
+
+    def set_grouping(self, grouped: bool):
+        """Grouped launches per pass over problems of one grid (default) or
+        one graph branch per problem (itp_batch_set_grouping)."""
+        _check_batch(self.b, load().itp_batch_set_grouping(self.b, 1 if grouped else 0))
+
+    @property
+    def groups(self):
+        return int(load().itp_batch_groups(self.b))
 
     def close(self):
         if self.b:

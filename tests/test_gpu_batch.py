@@ -36,11 +36,14 @@ def _batch(problems, prec):
     return b
 
 
+@pytest.mark.parametrize("grouped", [True, False])
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
-def test_batch_equals_single_problem_steps(prec):
-    """Each branch of the batch graph runs the same kernels on the same data
-    as that problem's own itp_step: energies and states agree exactly, and
-    the batch launches as many kernels as the single steps together."""
+def test_batch_equals_single_problem_steps(prec, grouped):
+    """Every CTA of a batch step computes what the problem's own itp_step
+    computes, whether the passes of problems with one grid run as grouped
+    launches or each problem is its own graph branch: energies and states
+    agree exactly.  The branch form launches as many kernels as the single
+    steps together; the grouped form fewer."""
     problems = _problems(5, (32, 48, 64), (3, 8))
     singles = []
     for g, V, psi in problems:
@@ -49,6 +52,7 @@ def test_batch_equals_single_problem_steps(prec):
         h.set_states(psi)
         singles.append(h)
     with _batch(problems, prec) as b:
+        b.set_grouping(grouped)
         for step in range(3):
             Eb = b.step(8, 0.25)
             l0 = [h.kernel_launches for h in singles]
@@ -57,7 +61,11 @@ def test_batch_equals_single_problem_steps(prec):
                 assert np.array_equal(Eb[p], Es[p]), (step, p)
             if step == 1:   # step 0 also built the tables, outside the graphs
                 per_step = sum(h.kernel_launches - a for h, a in zip(singles, l0))
-        assert b.kernel_launches == 3 * per_step
+        if grouped:
+            assert b.groups >= 1
+            assert b.kernel_launches < 3 * per_step
+        else:
+            assert b.kernel_launches == 3 * per_step
         for q, h in zip(b.problems, singles):
             assert np.array_equal(q.get_states(), h.get_states())
     for h in singles:
@@ -118,3 +126,23 @@ def test_batch_errors_name_the_problem():
         b[1].set_potential(problems[1][1])
         E = b.step(4, 0.2)   # usable after the error
         assert all(np.all(np.isfinite(e)) for e in E)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_grouped_batch_matches_branch_form(prec):
+    """Twelve problems on three grids (several per grid, uneven state counts):
+    grouped launches and the per-problem graph give the same energies and
+    states bit for bit, step after step, also for FP64 steps of a mixed
+    batch; three groups."""
+    problems = _problems(12, (32, 48, 64), (2, 9), seed=1400)
+    with _batch(problems, prec) as a, _batch(problems, prec) as c:
+        c.set_grouping(False)
+        for step in range(3):
+            fp64 = prec == "mixed" and step == 2
+            Ea = a.step(8, 0.25, fp64=fp64)
+            Ec = c.step(8, 0.25, fp64=fp64)
+            for p in range(len(problems)):
+                assert np.array_equal(Ea[p], Ec[p]), (step, p)
+        assert a.groups == 3 and c.groups == 0
+        for qa, qc in zip(a.problems, c.problems):
+            assert np.array_equal(qa.get_states(), qc.get_states())
