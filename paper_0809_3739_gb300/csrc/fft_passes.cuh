@@ -1695,6 +1695,18 @@ cudaError_t launch_plane(const GridDesc& g, const PlaneArgs<R>& a, cudaStream_t 
 
 template <typename R>
 cudaError_t launch_pencil(const GridDesc& g, const PencilArgs<R>& a, cudaStream_t st) {
+  if (g.pencil_w == 0) {
+    if constexpr (sizeof(R) == 4) {
+      return launch_pencil_tm(g, a, st);
+    } else {
+      // the FP64 passes of a mixed handle: the default slab width
+      GridDesc g2 = g;
+      const size_t full = (size_t)g.nz * g.nxh * 2 * sizeof(R), budget = 72 * 1024;
+      const int chunks = (int)((full + budget - 1) / budget);
+      g2.pencil_w = g2.pencil_pitch = (g.nxh + chunks - 1) / chunks;
+      return launch_pencil(g2, a, st);
+    }
+  }
   const size_t smem = pencil_smem_bytes(g, sizeof(R));
   switch (g.nz * 1000 + g.pencil_w) {
     case 32 * 1000 + 17: return pencil_dispatch<R, 32, 17>(g, a, smem, st);
@@ -1802,6 +1814,7 @@ template <typename R>
 cudaError_t launch_pencil_group(const GridDesc& g, int mode, const PencilArgs<R>* args,
                                 const int2* rows, int nrows, cudaStream_t st) {
   const size_t smem = pencil_smem_bytes(g, sizeof(R));
+  if (g.pencil_w < 1) return cudaErrorInvalidValue;
   switch (g.nz * 1000 + g.pencil_w) {
     case 32 * 1000 + 17: return pencil_group_dispatch<R, 32, 17>(g, mode, args, rows, nrows, smem, st);
     case 48 * 1000 + 25: return pencil_group_dispatch<R, 48, 25>(g, mode, args, rows, nrows, smem, st);

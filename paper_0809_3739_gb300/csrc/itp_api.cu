@@ -747,8 +747,10 @@ int set_tuning(itp_handle h, const int* t) {
   const int rb = pi == 0 ? 4 : 8;
   const int w = t[ITP_TUNE_PENCIL_W], split = t[ITP_TUNE_SPLIT], tb = t[ITP_TUNE_ROW_TB],
             chunks = t[ITP_TUNE_GRAM];
-  if (w < 1 || w > g.nxh || ((size_t)g.nz * w + g.nz) * 16 > kSmemLimit)
-    return fail(h, ITP_ERR_ARG, "pencil width %d not in 1..%d or too large", w, g.nxh);
+  if (w == 0 && !(pi == 0 && g.nz == 128))
+    return fail(h, ITP_ERR_ARG, "pencil width 0 (a column per thread) needs nz = 128 and FP32");
+  if (w < 0 || w > g.nxh || ((size_t)g.nz * w + g.nz) * 16 > kSmemLimit)
+    return fail(h, ITP_ERR_ARG, "pencil width %d not in 0..%d or too large", w, g.nxh);
   if (split < 0 || split > 3) return fail(h, ITP_ERR_ARG, "plane form must be 0, 1, 2 or 3");
   if (!split && plane_smem_bytes(g, rb) > kSmemLimit)
     return fail(h, ITP_ERR_ARG, "a %dx%d plane does not fit one CTA", g.nx, g.ny);
@@ -849,8 +851,9 @@ int autotune_lane(itp_handle h, int k, double tau, std::string& rep) {
     float best_ms = 1e30f;
     int last = -1;
     rep += "; pencil_w:";
-    for (int c = 1; c <= 4; ++c) {
-      const int w = (g.nxh + c - 1) / c;
+    for (int c = 0; c <= 4; ++c) {
+      const int w = c == 0 ? 0 : (g.nxh + c - 1) / c;
+      if (c == 0 && !(pi == 0 && g.nz == 128)) continue;
       if (w == last) continue;
       last = w;
       memcpy(cur, best, sizeof(cur));
@@ -1154,7 +1157,8 @@ int record_step(itp_handle h, int k, double tau, int flags, std::vector<RecOp>* 
 // A recorded pass that can run as a grouped launch: every FFT pass except
 // plane passes on planes too large for one CTA (row + column passes).
 bool groupable(const RecOp& op, itp_handle h) {
-  return op.kind != RecOp::kOther && !(op.kind == RecOp::kPlane && h->g.split_planes[op.lane]);
+  return op.kind != RecOp::kOther && !(op.kind == RecOp::kPlane && h->g.split_planes[op.lane]) &&
+         !(op.kind == RecOp::kPencil && h->g.pencil_w == 0);
 }
 
 // Grid, precision lane and launch shapes of a problem, and the kinds and

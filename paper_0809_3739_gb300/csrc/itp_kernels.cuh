@@ -13,7 +13,8 @@ struct GridDesc {
   long long n_points;        // nx*ny*nz
   long long n_half;          // nz*ny*nxh (complex)
   int pp;                    // shared-memory pitch of a row pair (complex, odd)
-  int pencil_w;              // kx columns per pencil CTA
+  int pencil_w;              // kx columns per pencil CTA; 0: one thread per
+                             // column, in TMEM (nz = 128, FP32)
   int pencil_pitch;          // shared-memory pitch of a pencil z-row (complex)
   // planes too large for one CTA run as row + column passes; per precision
   // (index 0: FP32, 1: FP64)
@@ -122,6 +123,9 @@ cudaError_t launch_plane(const GridDesc& g, const PlaneArgs<R>& a, cudaStream_t 
                          int* nlaunch = nullptr);
 template <typename R>
 cudaError_t launch_pencil(const GridDesc& g, const PencilArgs<R>& a, cudaStream_t st);
+// The pencil pass with one thread per z column and the column held in TMEM
+// (nz = 128, FP32; GridDesc::pencil_w = 0 selects it in launch_pencil).
+cudaError_t launch_pencil_tm(const GridDesc& g, const PencilArgs<float>& a, cudaStream_t st);
 
 // Factor tables of one term, tau_i = tau / i:
 //   f_half = exp(-tau_i V / 2), f_full = exp(-tau_i V)   ([N] each, precision R)

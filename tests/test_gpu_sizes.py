@@ -64,9 +64,12 @@ def _plane_forms(g, prec):
 
 
 def _pencil_widths(g):
-    """The widths itp_autotune tries: nx/2+1 columns cut into 1..4 blocks."""
+    """The widths itp_autotune tries: nx/2+1 columns cut into 1..4 blocks,
+    and 0 (one thread per column) where nz = 128 (FP32 only: set_tuning
+    refuses it for FP64)."""
     nxh = g.nx // 2 + 1
-    return sorted({-(-nxh // c) for c in (1, 2, 3, 4)}, reverse=True)
+    widths = sorted({-(-nxh // c) for c in (1, 2, 3, 4)}, reverse=True)
+    return widths + [0] if g.nz == 128 else widths   # 0: a column per thread, in TMEM
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -148,6 +151,44 @@ def test_every_launch_shape_at_full_edge(edge, prec):
                 report(f"{edge}^3 {prec} energies split={split} tb={tb} w={w}", err,
                        ENERGY_TOL[prec])
                 assert err < ENERGY_TOL[prec], (split, tb, w)
+
+
+def test_tmem_pencil_on_ragged_columns_matches_oracle():
+    """The pencil pass with one thread per z column (pencil width 0, nz =
+    128, its column held in TMEM) on a grid whose 3 x 24 x 25 = 1800 columns
+    end in a partly filled 128-thread tile: propagation at order 6 (both
+    propagating pencil forms of the expansion's terms), the energies (kinetic
+    pencil), and the mixed handle's FP64 evaluation, whose FP64 pencils fall
+    back to the default slab width."""
+    g = Grid(48, 24, 128, 14.0, 10.0, 40.0)
+    V = wells_problem(g)
+    m = 3
+    psi = seeded_states(g, m, seed=91)
+    order, tau = 6, 0.3
+    phi_ref = O.propagate(psi, V, g, order, tau)
+    psi0, _ = O.cholesky_orthonormalize(psi, g.dV)
+    E_ref, _, _ = O.energies(psi0, V, g, ritz=False)
+    tol = propagate_tolerance(order, g.n_points, "mixed")
+    with P.ItpGrid(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, m, 0, P.ITP_MIXED) as h:
+        h.set_potential(V)
+        t = h.get_tuning()
+        h.set_tuning(0, t["split"], t["row_tb"], t["gram_ctas"])
+        assert h.get_tuning()["pencil_w"] == 0
+        h.set_states(psi)
+        h.propagate(order, tau)
+        err = _relerr(h.get_phi(), phi_ref)
+        report(f"48x24x128 mixed propagate order {order} w=0", err, tol)
+        assert err < tol
+        h.set_states(psi0)
+        E = h.energies(False)
+        err = float(np.max(np.abs(E - E_ref)) / np.max(np.abs(E_ref)))
+        report("48x24x128 mixed energies w=0", err, ENERGY_TOL["mixed"])
+        assert err < ENERGY_TOL["mixed"]
+        E64 = h.energies(False, fp64=True)
+        E_ref64, _, _ = O.energies(h.get_states(), V, g, ritz=False)
+        err = float(np.max(np.abs(E64 - E_ref64)) / np.max(np.abs(E_ref64)))
+        report("48x24x128 FP64 evaluation w=0", err, 1e-11)
+        assert err < 1e-11
 
 
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
