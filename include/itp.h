@@ -286,7 +286,10 @@ int itp_profile_read(itp_handle h, int kind, long long* launches, double* total_
  * ITP_MIXED, FP64 for ITP_FP64), as an int[ITP_TUNING_LEN]:
  *   [ITP_TUNE_PENCIL_W]  kx columns per pencil-pass CTA, 1..nx/2+1 (and the
  *                        FP64 pencil slab, nz*(w+1) complex doubles, within
- *                        one CTA's 227 KB of shared memory)
+ *                        one CTA's 227 KB of shared memory); 0: one thread
+ *                        per z column with the column held in tensor memory
+ *                        (nz = 128, FP32 lane only; the FP64 pencils of a
+ *                        mixed handle then take the default width)
  *   [ITP_TUNE_SPLIT]     plane-pass form: 0: one CTA per plane for the x
  *                        and y transforms (only where the plane fits one
  *                        CTA); 1: row passes (x) and column passes (y), three
