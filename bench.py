@@ -83,17 +83,15 @@ def make_inputs(w, rank=0):
 NCU_TRAFFIC = {
     # DRAM bytes (read + write) per full launch from one ncu capture of the
     # 16-state case, scaled by the number of states; valid only while the
-    # kernel's source file is the one that was profiled (the captures were
-    # taken before the passes moved into a header of their own, with the
-    # same kernel code)
-    ("c60_128", "plane_merged"): {"bytes": 1.791e9,
+    # kernel's source file is the one that was profiled
+    ("c60_128", "plane_merged"): {"bytes": 1.788e9,
                                   "source": "paper_0809_3739_gb300/csrc/fft_passes.cuh",
-                                  "sha1": "45c108a72460d4ffa0d8dfd74337bb4abb548216",
+                                  "sha1": "741c0a37f64df51f83118f3949fa0fdf1e24e3b3",
                                   "profile": "profiles/plane_merged_c60_128.md"},
-    ("c60_128", "pencil"): {"bytes": 1.721e9,
-                            "source": "paper_0809_3739_gb300/csrc/fft_passes.cuh",
-                            "sha1": "45c108a72460d4ffa0d8dfd74337bb4abb548216",
-                            "profile": "profiles/pencil_c60_128.md"},
+    ("c60_128", "pencil"): {"bytes": 1.697e9,
+                            "source": "paper_0809_3739_gb300/csrc/fft_tmem.cuh",
+                            "sha1": "5657d3abdd160f6831798c09342aa04ad0083a70",
+                            "profile": "profiles/pencil_tmem_c60_128.md"},
 }
 
 
