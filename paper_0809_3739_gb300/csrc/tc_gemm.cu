@@ -461,25 +461,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       aborted = true;
       break;
     }
-    pending |= 1u << s;
-    pend_parity = (pend_parity & ~(1u << s)) | ((uint32_t)((local >> 1) & 1) << s);
-    if (threadIdx.x == 0) {
-      tc_fence_after();
-      const uint32_t d = tmem + (uint32_t)(s * kApplyNT);
-#pragma unroll
-      for (int ks = 0; ks < 16; ++ks) {
-        const uint32_t koff = ks * 256;
-        const uint64_t dah = smem_desc(m_hi + koff, 128, sbo);
-        const uint64_t dal = smem_desc(m_lo + koff, 128, sbo);
-        const uint64_t dbh = smem_desc(xpart(s, 0) + koff, 128, sbo);
-        const uint64_t dbl = smem_desc(xpart(s, 1) + koff, 128, sbo);
-        mma_tf32(d, dah, dbh, idesc, ks > 0 ? 1u : 0u);
-        mma_tf32(d, dah, dbl, idesc, 1u);
-        mma_tf32(d, dal, dbh, idesc, 1u);
-      }
-      mma_commit(&bar[s]);
-    }
-    // epilogue of the previous tile (its MMAs ran while this tile staged)
+    // epilogue of the previous tile (its MMAs ran while this tile staged),
+    // then this tile's MMAs: issued before the epilogue, they kept the
+    // issuing thread's warp, and with it the epilogue's block barrier, waiting
     if (prev_tile >= 0) {
       const int ps = (local - 1) & 1;
       ok = mbar_wait(&bar[ps], (uint32_t)(((local - 1) >> 1) & 1), deadline);
@@ -490,6 +474,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         break;
       }
       pending &= ~(1u << ps);
+    }
+    pending |= 1u << s;
+    pend_parity = (pend_parity & ~(1u << s)) | ((uint32_t)((local >> 1) & 1) << s);
+    if (threadIdx.x == 0) {
+      tc_fence_after();
+      const uint32_t d = tmem + (uint32_t)(s * kApplyNT);
+      // descriptors of the k-slices: the start-address field (bits 0-13,
+      // address / 16) advances by 256 / 16 per slice of 8 K values
+      const uint64_t ah = smem_desc(m_hi, 128, sbo), al = smem_desc(m_lo, 128, sbo);
+      const uint64_t bh = smem_desc(xpart(s, 0), 128, sbo), bl = smem_desc(xpart(s, 1), 128, sbo);
+#pragma unroll
+      for (int ks = 0; ks < 16; ++ks) {
+        const uint64_t step = (uint64_t)(ks * 16);
+        mma_tf32(d, ah + step, bh + step, idesc, ks > 0 ? 1u : 0u);
+        mma_tf32(d, ah + step, bl + step, idesc, 1u);
+        mma_tf32(d, al + step, bh + step, idesc, 1u);
+      }
+      mma_commit(&bar[s]);
     }
     prev_tile = tile;
 #pragma unroll
