@@ -146,3 +146,40 @@ def test_grouped_batch_matches_branch_form(prec):
         assert a.groups == 3 and c.groups == 0
         for qa, qc in zip(a.problems, c.problems):
             assert np.array_equal(qa.get_states(), qc.get_states())
+
+
+def test_batch_with_tmem_pencils_equals_single_problem_steps():
+    """Problems with nz = 128 whose pencil width is 0 (one thread per z
+    column, the column in TMEM) take part in a grouped batch: their pencil
+    passes run as per-problem launches (the TMEM pencil has no grouped
+    form), the plane passes of the two problems on one grid as grouped
+    launches; energies and states equal the problems' own graph steps with
+    the same launch shapes, bit for bit."""
+    from gpu_helpers import seeded_states, wells_problem
+    from itp_workloads import Grid
+
+    grids = [Grid(48, 24, 128, 14.0, 10.0, 40.0), Grid(48, 24, 128, 14.0, 10.0, 40.0),
+             Grid(32, 32, 128, 12.0, 12.0, 40.0)]
+    problems = [(g, wells_problem(g), seeded_states(g, 3 + p, seed=300 + p))
+                for p, g in enumerate(grids)]
+    singles = []
+    for g, V, psi in problems:
+        h = P.ItpGrid(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, psi.shape[0], 0, P.ITP_MIXED)
+        h.set_potential(V)
+        h.set_states(psi)
+        t = h.get_tuning()
+        h.set_tuning(0, t["split"], t["row_tb"], t["gram_ctas"])
+        singles.append(h)
+    with _batch(problems, "mixed") as b:
+        for q in b.problems:
+            t = q.get_tuning()
+            q.set_tuning(0, t["split"], t["row_tb"], t["gram_ctas"])
+        for step in range(2):
+            Eb = b.step(8, 0.25)
+            Es = [h.step_graph(8, 0.25) for h in singles]
+            for p in range(len(problems)):
+                assert np.array_equal(Eb[p], Es[p]), (step, p)
+        for q, h in zip(b.problems, singles):
+            assert np.array_equal(q.get_states(), h.get_states())
+    for h in singles:
+        h.close()
