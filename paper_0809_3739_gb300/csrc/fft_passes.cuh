@@ -447,6 +447,16 @@ __device__ __forceinline__ void xB_inv_merge_r(const PlaneGeo<R, NX, NY, NTT>& G
   const int grp = lane / r2, b = lane - grp * r2;
   const int ngroups = (G.npair + rpw - 1) / rpw;
   const int half = G.nx >> 1;
+  // the twiddles w^{-i b} depend on the lane only: for R1 <= 8 they are
+  // loaded once into registers, not per row group (the row loop writes the
+  // same shared array, so the compiler reloads them); at R1 = 16 the 30 more
+  // registers would spill
+  constexpr bool kHold = R1 <= 8;
+  C twr[kHold ? R1 : 1];
+  if constexpr (kHold) {
+#pragma unroll
+    for (int i = 1; i < R1; ++i) twr[i] = tw[i * b];
+  }
   for (int rg = warp; rg < ngroups; rg += NW) {
     const int t = rg * rpw + grp;
     const bool active = grp < rpw && t < G.npair;
@@ -474,7 +484,10 @@ __device__ __forceinline__ void xB_inv_merge_r(const PlaneGeo<R, NX, NY, NTT>& G
     Dft<R1, 1, C>::run(v);
     if (R1 > 1) {
 #pragma unroll
-      for (int i = 1; i < R1; ++i) v[i] = cmulc(v[i], tw[i * b]);
+      for (int i = 1; i < R1; ++i) {
+        if constexpr (kHold) v[i] = cmulc(v[i], twr[i]);
+        else v[i] = cmulc(v[i], tw[i * b]);
+      }
     }
     if (active) {
 #pragma unroll
