@@ -143,6 +143,32 @@ __device__ __forceinline__ float2 cmulri<float2>(float2 a, float2 f) {
   return __fmul2_rn(a, f);
 }
 
+// a[j] *= w^(q j) (CONJ: w^(-q j)), j = 1..R-1, from the table tw of
+// roots.  For R = 8 and 16 the factor is w^(q j1) w^(4 q j2) with
+// j = j1 + 4 j2: four or six table reads instead of seven or fifteen (the
+// reads are shared-memory wavefronts, the passes' bound), each product
+// within about an ulp of the table value.
+template <int R, bool CONJ = false, typename C>
+__device__ __forceinline__ void twiddle_stage(C (&a)[R], const C* tw, int q) {
+  if constexpr (R == 8 || R == 16) {
+    constexpr int NH = R / 4;   // hi factors w^(4 q j2), j2 = 1 .. NH-1
+    C lo[4], hi[NH];
+#pragma unroll
+    for (int j = 1; j < 4; ++j) lo[j] = tw[q * j];
+#pragma unroll
+    for (int j = 1; j < NH; ++j) hi[j] = tw[4 * q * j];
+#pragma unroll
+    for (int j = 1; j < R; ++j) {
+      const int j1 = j & 3, j2 = j >> 2;
+      const C w = j2 == 0 ? lo[j1] : (j1 == 0 ? hi[j2] : cmul(lo[j1], hi[j2]));
+      a[j] = CONJ ? cmulc(a[j], w) : cmul(a[j], w);
+    }
+  } else {
+#pragma unroll
+    for (int j = 1; j < R; ++j) a[j] = CONJ ? cmulc(a[j], tw[q * j]) : cmul(a[j], tw[q * j]);
+  }
+}
+
 // ----------------------------------------------------------------------------
 // Shared-memory geometry of one plane.
 template <typename R, int NX, int NY, int NTT>
@@ -220,7 +246,7 @@ __device__ __forceinline__ void xA_fwd_global_r(const PlaneGeo<R, NX, NY, NTT>& 
       if (f) a[j] = cmulri(a[j], __ldg(&f[x * G.gpair + t]));
     }
     Dft<R2, -1, C>::run(a);
-    if (G.ax.r1 > 1) {
+    if (G.ax.r1 > 1) {   // (the two-table twiddles measured slower here)
 #pragma unroll
       for (int j = 1; j < R2; ++j) a[j] = cmul(a[j], tw[n1 * j]);
     }
@@ -281,10 +307,7 @@ __device__ __forceinline__ void xA_inv_then_r(const PlaneGeo<R, NX, NY, NTT>& G,
     Dft<R2, 1, C>::run(a);
     if (epi.template apply<R2>(t, n1, a)) {
       Dft<R2, -1, C>::run(a);
-      if (G.ax.r1 > 1) {
-#pragma unroll
-        for (int j = 1; j < R2; ++j) a[j] = cmul(a[j], tw[n1 * j]);
-      }
+      if (G.ax.r1 > 1) twiddle_stage<R2>(a, tw, n1);
 #pragma unroll
       for (int j = 0; j < R2; ++j) sm[G.rowA(t, n1, j)] = a[j];
     }
@@ -528,10 +551,7 @@ __device__ __forceinline__ void yB_inv_global_r(const PlaneGeo<R, NX, NY, NTT>& 
 #pragma unroll
     for (int i = 0; i < R1; ++i) a[i] = spec[(b + G.ay.r2 * i) * G.srs + t];
     Dft<R1, 1, C>::run(a);
-    if (R1 > 1) {
-#pragma unroll
-      for (int i = 1; i < R1; ++i) a[i] = cmulc(a[i], tw[i * b]);
-    }
+    if (R1 > 1) twiddle_stage<R1, true>(a, tw, b);
 #pragma unroll
     for (int i = 0; i < R1; ++i) sm[G.colB(t, b, i)] = a[i];
   });
@@ -551,10 +571,7 @@ __device__ __forceinline__ void yA_r(const PlaneGeo<R, NX, NY, NTT>& G, C* sm, c
 #pragma unroll
     for (int j = 0; j < R2; ++j) a[j] = sm[G.colA(t, n1, j)];
     Dft<R2, DIR, C>::run(a);
-    if (DIR < 0 && G.ay.r1 > 1) {
-#pragma unroll
-      for (int j = 1; j < R2; ++j) a[j] = cmul(a[j], tw[n1 * j]);
-    }
+    if (DIR < 0 && G.ay.r1 > 1) twiddle_stage<R2>(a, tw, n1);
 #pragma unroll
     for (int j = 0; j < R2; ++j) sm[G.colA(t, n1, j)] = a[j];
   });
