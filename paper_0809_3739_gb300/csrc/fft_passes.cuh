@@ -91,6 +91,12 @@ __host__ __device__ constexpr int min_blocks(long long smem_bytes, int cap) {
 __host__ __device__ constexpr long long plane_smem_ct(int nx, int ny, int rbytes) {
   return nx ? ((long long)(ny / 2) * row_pitch(nx) + nx + ny) * 2 * rbytes : 0;
 }
+// CTAs per SM a specialised pencil pass asks the compiler to fit (the
+// register budget follows): 3 for FP32, but 2 for 256-point pencils, whose
+// radix-16 stages do not fit the 75 registers of three 288-thread CTAs.
+__host__ __device__ constexpr int pencil_min_ctas(int nz, int rbytes) {
+  return rbytes == 4 && nz < 256 ? 3 : 2;
+}
 __host__ __device__ constexpr long long pencil_smem_ct(int nz, int w, int rbytes) {
   return nz ? ((long long)nz * w + nz) * 2 * rbytes : 0;
 }
@@ -1406,7 +1412,7 @@ __device__ __forceinline__ void pencil_body(const GridDesc& g, const PencilArgs<
 template <typename R, int NZ, int W, int MODE>
 __global__ void __launch_bounds__(launch_threads(task_threads(W)),
                                   min_blocks(pencil_smem_ct(NZ, W, sizeof(R)),
-                                             sizeof(R) == 4 ? 3 : 2))
+                                             pencil_min_ctas(NZ, sizeof(R))))
     pencil_kernel(const GridDesc g, const PencilArgs<R> a) {
   pencil_body<R, NZ, W, MODE>(g, a, blockIdx.x, blockIdx.y);
 }
@@ -1415,7 +1421,7 @@ __global__ void __launch_bounds__(launch_threads(task_threads(W)),
 template <typename R, int NZ, int W, int MODE>
 __global__ void __launch_bounds__(launch_threads(task_threads(W)),
                                   min_blocks(pencil_smem_ct(NZ, W, sizeof(R)),
-                                             sizeof(R) == 4 ? 3 : 2))
+                                             pencil_min_ctas(NZ, sizeof(R))))
     pencil_group_kernel(const GridDesc g, const PencilArgs<R>* __restrict__ args,
                         const int2* __restrict__ rows) {
   const int2 r = rows[blockIdx.y];
