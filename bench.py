@@ -84,9 +84,9 @@ NCU_TRAFFIC = {
     # DRAM bytes (read + write) per full launch from one ncu capture of the
     # 16-state case, scaled by the number of states; valid only while the
     # kernel's source file is the one that was profiled
-    ("c60_128", "plane_merged"): {"bytes": 1.788e9,
+    ("c60_128", "plane_merged"): {"bytes": 1.784e9,
                                   "source": "paper_0809_3739_gb300/csrc/fft_passes.cuh",
-                                  "sha1": "741c0a37f64df51f83118f3949fa0fdf1e24e3b3",
+                                  "sha1": "6982298585d4fd2f311b2719a76cc47cd560377c",
                                   "profile": "profiles/plane_merged_c60_128.md"},
     ("c60_128", "pencil"): {"bytes": 1.697e9,
                             "source": "paper_0809_3739_gb300/csrc/fft_tmem.cuh",
