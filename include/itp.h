@@ -387,7 +387,10 @@ long long itp_batch_kernel_launches(itp_batch_handle b);
  * (overlap, Cholesky, update, eigenvalues, copies) run as parallel branches
  * between those launches; groups run as parallel branches.  Every CTA
  * computes exactly what the problem's own launch would, so results are the
- * same bit for bit.  grouped == 0: one branch of ~50 launches per problem.
+ * same bit for bit.  Passes without a grouped form run per problem inside
+ * the group: plane passes of row + column or cluster planes, and pencils of
+ * width 0 (ITP_TUNE_PENCIL_W).  grouped == 0: one branch of ~50 launches
+ * per problem.
  * Takes effect at the next itp_batch_step (which captures a new graph).
  * Returns ITP_OK or ITP_ERR_ARG (null batch). */
 int itp_batch_set_grouping(itp_batch_handle b, int grouped);
