@@ -428,72 +428,133 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const double* __restrict__
 
 // ---------------------------------------------------------------------------
 // Eigenvalues only: the cluster tridiagonalisation above, then bisection on
-// Sturm counts with one warp per eigenvalue (32-point multisection), one
-// warp per CTA so that the FP64 work spreads over as many SMs as there are
-// eigenvalues.
-// Number of eigenvalues of the tridiagonal (d, e) below x (Sturm count of
-// the LDL^T pivots, with the usual guard against a zero pivot).
-__device__ __forceinline__ int sturm_count(const double* d, const double* e2, int m, double x,
-                                           double pivmin) {
-  int cnt = 0;
-  double q = d[0] - x;
-  if (fabs(q) < pivmin) q = -pivmin;
-  cnt += q < 0.0;
+// Sturm counts, one CTA of four warps per eigenvalue (128-point
+// multisection: seven bits per round, one warp on each of the SM's four
+// sub-partitions, whose FP64 units the counts keep busy).
+constexpr int kBisWarps = 4;
+constexpr int kBisPts = 32 * kBisWarps;   // points per round; the last is hi
+
+// Biased binary exponent of a double (0 for zero and subnormals).
+__device__ __forceinline__ int dexp(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
+// v * 2^k by its exponent field (v normal, the result normal).
+__device__ __forceinline__ double dscale(double v, int k) {
+  return __hiloint2double(__double2hiint(v) + (k << 20), __double2loint(v));
+}
+
+// Number of eigenvalues below x of the symmetric tridiagonal with diagonal
+// d and squared off-diagonal e2 (e2[i] couples rows i and i+1), scaled so
+// that |d_i|, |x| < 1 and e2_i <= 4.  The sign changes of the leading
+// principal minors of T - x I,
+//   p_0 = 1,  p_1 = d_0 - x,  p_{i+1} = (d_i - x) p_i - e2_{i-1} p_{i-1},
+// i.e. the negative pivots p_{i+1}/p_i of its LDL^T factorisation.  No
+// division: three FP64 operations per row, the rest on the integer pipe.
+//  - A minor that vanishes against the previous one (|p_{i+1}| < 2^-599
+//    |p_i|, zero included) becomes -2^-600 p_i: the pivot -2^-600, as a
+//    zero pivot of the LDL^T recurrence is replaced by a tiny negative one.
+//  - p_i and p_{i-1} are rescaled together by a power of two (exponent
+//    arithmetic, exact) whenever |p_i| leaves [2^-256, 2^257).
+// With the pivot rule |p_{i-1}| <= 2^600 |p_i|, so |p_{i+1}| < 2^603 |p_i|
+// and every value stays a normal double between 2^-860 and 2^860.
+__device__ __forceinline__ int sturm_count(const double* __restrict__ d,
+                                           const double* __restrict__ e2, int m, double x) {
+  double pm = 1.0, p = d[0] - x;
+  int ep = dexp(p);
+  if (ep < 1023 - 599) {
+    p = -0x1p-600;
+    ep = 1023 - 600;
+  }
+  int cnt = __double2hiint(p) < 0;
+  if (ep < 1023 - 256) {
+    p = dscale(p, 1023 - ep);
+    pm = dscale(pm, 1023 - ep);
+    ep = 1023;
+  }
   for (int i = 1; i < m; ++i) {
-    q = d[i] - x - e2[i - 1] / q;
-    if (fabs(q) < pivmin) q = -pivmin;
-    cnt += q < 0.0;
+    double pn = fma(d[i] - x, p, -(e2[i - 1] * pm));
+    int en = dexp(pn);
+    if (en < ep - 599) {
+      pn = __hiloint2double((__double2hiint(p) ^ (int)0x80000000) - (600 << 20),
+                            __double2loint(p));
+      en = ep - 600;
+    }
+    cnt += (__double2hiint(pn) ^ __double2hiint(p)) < 0;
+    pm = p;
+    p = pn;
+    ep = en;
+    if ((unsigned)(en - (1023 - 256)) > 512u) {
+      p = dscale(p, 1023 - en);
+      pm = dscale(pm, 1023 - en);
+      ep = 1023;
+    }
   }
   return cnt;
 }
 
-// One warp per eigenvalue index j: 32-point multisection of a bracket of
-// the j-th smallest eigenvalue down to a few ulps.
-__global__ void __launch_bounds__(32) bisect_kernel(const double* __restrict__ dg,
-                                                     const double* __restrict__ eg, int m,
-                                                     double* __restrict__ E) {
+// One CTA per eigenvalue index j (ascending): the Gershgorin interval of
+// the tridiagonal, scaled by a power of two into (-1, 1), narrowed by
+// 128-point multisection down to a few ulps.
+__global__ void __launch_bounds__(kBisPts) bisect_kernel(const double* __restrict__ dg,
+                                                          const double* __restrict__ eg, int m,
+                                                          double* __restrict__ E) {
   __shared__ double sd[kMaxM], se2[kMaxM];
-  __shared__ double s_lo, s_hi, s_pivmin;
-  const int tid = threadIdx.x;
-  for (int i = tid; i < m; i += blockDim.x) {
-    sd[i] = dg[i];
-    se2[i] = i + 1 < m ? eg[i] * eg[i] : 0.0;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double lo = sd[0], hi = sd[0], emax = 0.0;
-    for (int i = 0; i < m; ++i) {
-      const double r = (i > 0 ? sqrt(se2[i - 1]) : 0.0) + (i + 1 < m ? sqrt(se2[i]) : 0.0);
-      lo = fmin(lo, sd[i] - r);
-      hi = fmax(hi, sd[i] + r);
-      if (i + 1 < m) emax = fmax(emax, se2[i]);
+  __shared__ double s_lo, s_hi, s_scale;
+  __shared__ unsigned s_ball[2][kBisWarps];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (warp == 0) {
+    double lo = dg[0], hi = dg[0];
+    for (int i = lane; i < m; i += 32) {
+      const double r = (i > 0 ? fabs(eg[i - 1]) : 0.0) + (i + 1 < m ? fabs(eg[i]) : 0.0);
+      lo = fmin(lo, dg[i] - r);
+      hi = fmax(hi, dg[i] + r);
     }
-    const double span = fmax(hi - lo, 1e-300);
-    s_lo = lo - 1e-14 * span - 1e-300;
-    s_hi = hi + 1e-14 * span + 1e-300;
-    s_pivmin = fmax(1e-300, 2.2250738585072014e-308 * fmax(1.0, emax));
+    for (int o = 16; o; o >>= 1) {
+      lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
+      const double span = fmax(hi - lo, 1e-300);
+      lo -= 1e-14 * span + 1e-300;
+      hi += 1e-14 * span + 1e-300;
+      int k;
+      frexp(fmax(fabs(lo), fabs(hi)), &k);   // max |.| = f 2^k, f in [1/2, 1)
+      const double g = ldexp(1.0, -k);
+      s_scale = g;
+      s_lo = lo * g;
+      s_hi = hi * g;
+    }
   }
   __syncthreads();
-  const int lane = tid & 31;
-  const int j = blockIdx.x * (blockDim.x >> 5) + (tid >> 5);
-  if (j >= m) return;
+  const double g = s_scale;
+  for (int i = tid; i < m; i += blockDim.x) {
+    sd[i] = dg[i] * g;
+    const double ei = i + 1 < m ? eg[i] * g : 0.0;
+    se2[i] = ei * ei;
+  }
+  __syncthreads();
+  const int j = blockIdx.x;
   double lo = s_lo, hi = s_hi;
-  const double pivmin = s_pivmin;
-  for (int it = 0; it < 24; ++it) {
+  for (int it = 0; it < 16; ++it) {
     const double width = hi - lo;
-    if (width <= 4.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi)) + pivmin) break;
-    // 31 interior points split [lo, hi] into 32 parts
-    const double x = lo + width * (double)(lane + 1) / 32.0;
-    const int c = lane < 31 ? sturm_count(sd, se2, m, x, pivmin) : m + 1;
-    // the eigenvalue j lies in the first part whose right end has count > j
+    if (width <= 4.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi)) + 0x1p-70) break;
+    // points lo + width (t+1)/128, t < 127; point 127 is hi (count m + 1)
+    const double x = lo + width * (double)(tid + 1) / (double)kBisPts;
+    const int c = tid < kBisPts - 1 ? sturm_count(sd, se2, m, x) : m + 1;
     const unsigned ball = __ballot_sync(0xffffffffu, c > j);
-    const int first = __ffs(ball) - 1;   // 0..31 (lane 31 always votes)
-    const double nlo = first == 0 ? lo : lo + width * (double)first / 32.0;
-    const double nhi = first == 31 ? hi : lo + width * (double)(first + 1) / 32.0;
+    if (lane == 0) s_ball[it & 1][warp] = ball;
+    __syncthreads();
+    // the eigenvalue j lies in the first part whose right end has count > j
+    int first = kBisPts - 1;
+    for (int w = kBisWarps - 1; w >= 0; --w) {
+      const unsigned b = s_ball[it & 1][w];
+      if (b) first = 32 * w + __ffs(b) - 1;
+    }
+    const double nlo = first == 0 ? lo : lo + width * (double)first / (double)kBisPts;
+    const double nhi =
+        first == kBisPts - 1 ? hi : lo + width * (double)(first + 1) / (double)kBisPts;
     lo = nlo;
     hi = nhi;
   }
-  if (lane == 0) E[j] = 0.5 * (lo + hi);
+  if (tid == 0) E[j] = 0.5 * (lo + hi) / g;
 }
 
 __global__ void diag_kernel(const double* __restrict__ H, int m, double* __restrict__ E) {
@@ -696,7 +757,7 @@ cudaError_t launch_tridiag(const double* H, int m, double* work, cudaStream_t st
 
 cudaError_t launch_bisect(const double* work, int m, double* E, cudaStream_t st) {
   if (m > kMaxM) return cudaErrorInvalidValue;
-  bisect_kernel<<<m, 32, 0, st>>>(work, work + m, m, E);
+  bisect_kernel<<<m, kBisPts, 0, st>>>(work, work + m, m, E);
   return cudaGetLastError();
 }
 
